@@ -1,0 +1,173 @@
+/*
+ * wri.h -- C ABI of libwri: the per-source, per-frequency hot path of source-free
+ * Wavefield Reconstruction Inversion (arXiv 2410.18429) on one NVIDIA GB300 (sm_103a).
+ *
+ * The library solves, for every (source i, frequency j) system of a batch, the
+ * augmented least-squares problem of Eqs. ObjPen / CmpctWRIobj / Sandb,
+ *
+ *     min_u  1/2 || Z A_j u - b1 ||^2 + 1/2 lambda^2 || P_i u - d_ij ||^2 ,
+ *
+ * with the matrix-free Helmholtz operator A_j = omega_j^2 diag(w m) + L_pml
+ * (Sec. "3D Source free WRI": A = omega^2 diag(m) + Laplacian, plus a stretched-
+ * coordinate absorbing layer), estimates the source weight a = (A u)[src]
+ * (Eq. SimpObj, second block row) and accumulates the model gradient of Eq. VarG2.
+ *
+ *   source-free mode (alpha == NULL):  Z = I - e e^H,  b1 = 0           (Eq. SimpObj)
+ *   known-weight mode (alpha != NULL): Z = I,          b1 = alpha e     (Eq. ObjPen)
+ *
+ * Conventions shared by every entry point
+ *   - lambda weights the DATA term (the paper's lambda_p on the PDE term is 1/lambda);
+ *     the minimiser is the same as the paper's.
+ *   - Grids are C-ordered [nz][ny][nx], x fastest; node index (k*ny + j)*nx + i.
+ *     nx, ny, nz count the computational nodes INCLUDING npml padding cells per face.
+ *   - Complex arrays are interleaved (re, im): float2 for WRI_C64, double2 for WRI_C128.
+ *     Real arrays (m) are float for WRI_C64 and double for WRI_C128.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host" pointers
+ *     are ordinary host memory read before the call returns.  The library never
+ *     allocates device memory: scratch comes from the caller's workspace.
+ *   - Every call enqueues its work on `stream` (a cudaStream_t; 0 is the legacy
+ *     default stream).  wri_solve_batch additionally waits on the host for the
+ *     stopping decision (it polls a device counter every few iterations).
+ *   - Return value: WRI_OK or an error code (wri_strerror).  Argument errors are
+ *     detected before any work is enqueued.  Per-system outcomes go to device arrays.
+ */
+#ifndef WRI_H
+#define WRI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* wri_stream_t; /* identical to cudaStream_t */
+
+#if defined(__GNUC__)
+#define WRI_API __attribute__((visibility("default")))
+#else
+#define WRI_API
+#endif
+
+/* return codes */
+#define WRI_OK 0
+#define WRI_EINVAL 1      /* invalid argument (null pointer, size, index out of range, ...) */
+#define WRI_ECUDA 2       /* a CUDA launch or runtime call failed */
+#define WRI_EWORKSPACE 3  /* workspace pointer null, misaligned (256 B) or too small */
+#define WRI_ENOTSUP 4     /* valid but unsupported combination of options */
+
+/* per-system status written by wri_solve_batch */
+#define WRI_SYS_OK 0         /* relative normal-equation residual <= tol */
+#define WRI_SYS_MAXITER 1    /* max_iter reached before tol */
+#define WRI_SYS_BREAKDOWN 2  /* ||S p|| = 0 with a non-zero residual (cannot progress) */
+#define WRI_SYS_NONFINITE 3  /* a NaN/Inf appeared in a step length or norm */
+
+/* arithmetic of the iterative solve */
+#define WRI_C64 0   /* complex64 vectors and stencil, FP64 inner products and scalars */
+#define WRI_C128 1  /* complex128 throughout */
+
+/* Grid of one frequency group.  Stretch factor of the absorbing layer on each axis
+ * (our reading; the paper states no boundary condition):
+ *   s(xi) = 1 + i sigma(xi)/omega,  sigma = sigma_max (xi/L)^2,  L = npml*h,
+ *   sigma_max = 3 v_max ln(1/pml_R) / (2 L),  xi = distance into the layer. */
+typedef struct {
+  int32_t nx, ny, nz; /* computational nodes per axis, >= 3 each, including padding */
+  int32_t npml;       /* padding cells per face (0 = no absorbing layer, Dirichlet box) */
+  double h;           /* grid spacing (m), > 0 */
+  double omega;       /* angular frequency omega_j (rad/s), > 0 */
+  double pml_R;       /* target reflection of the layer, in (0, 1) */
+  double v_max;       /* velocity (m/s) that sets sigma_max, > 0 */
+} wri_grid;
+
+/* One group of systems sharing a grid, a frequency and a model (a "grouped
+ * inversion" block of Eq. Mmatrix2, read as block diagonal). */
+typedef struct {
+  wri_grid grid;
+  const void* m;            /* device [n] squared slowness (float | double per dtype) */
+  int32_t nsys;             /* systems in the group, >= 1 */
+  const int64_t* src_idx;   /* host [nsys] source node of each system */
+  const int32_t* rec_off;   /* host [nsys+1] CSR offsets into rec_idx / d, rec_off[0] = 0 */
+  const int32_t* rec_idx;   /* host [rec_off[nsys]] receiver nodes; distinct within a system */
+  const void* d;            /* device [rec_off[nsys]] observed data (complex, dtype) */
+  const double* alpha;      /* device [2*nsys] known weights (complex128) or NULL = source-free */
+  double lambda;            /* data weight, > 0 */
+  void* u;                  /* device [nsys][n] complex (dtype): in = x0 if warm_start, out = u */
+} wri_group;
+
+typedef struct {
+  double tol;          /* stop when ||S^H (b - S u)|| <= tol ||S^H b||  (tol >= 0) */
+  int32_t max_iter;    /* iteration cap per system (per inner solve when refining), >= 1 */
+  int32_t dtype;       /* WRI_C64 or WRI_C128 */
+  int32_t warm_start;  /* 1: start from the values in u; 0: start from u = 0 */
+  int32_t max_refine;  /* WRI_C64 only: > 0 enables FP64 iterative refinement, at most this
+                          many outer corrections; each inner FP32 solve runs to inner_tol */
+  double refine_tol;   /* refinement stops when the FP64 relative residual <= refine_tol */
+  double inner_tol;    /* relative tolerance of each inner FP32 solve (e.g. 1e-3) */
+  int32_t plain;       /* 1: unbatched, unfused baseline (one system at a time, separate
+                          BLAS-1 kernels, scalars read back by the host every iteration) */
+  int32_t poll_every;  /* iterations launched between host polls of the done-counter
+                          (0 = library default) */
+  int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
+  int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
+} wri_solve_opts;
+
+/* y = A x (wri_apply_A) or y = A^H x (wri_apply_AH) for `nsys` vectors that share the
+ * grid and model: x, y device [nsys][n] complex (dtype), m device [n] real (dtype).
+ * x and y must not overlap.  Operator: Sec. "3D Source free WRI", first paragraph.
+ * A is complex symmetric, so A^H x = conj(A conj(x)). */
+WRI_API int wri_apply_A(const wri_grid* grid, int dtype, const void* m, int nsys, const void* x, void* y,
+                wri_stream_t stream);
+WRI_API int wri_apply_AH(const wri_grid* grid, int dtype, const void* m, int nsys, const void* x, void* y,
+                 wri_stream_t stream);
+
+/* Bytes of device workspace wri_solve_batch needs for these groups and options
+ * (0 on invalid arguments).  The workspace must be 256-byte aligned. */
+WRI_API size_t wri_workspace_size(const wri_group* groups, int ngroups, const wri_solve_opts* opts);
+
+/* Solve every system of every group (the LSQR/CG solve of Eq. SimpObj, Algorithm 1
+ * read as CGLS, grouped as in Eq. Mmatrix2 with per-system scalars).
+ *   iters  device [sum nsys] int32   iterations per system (summed over refinements)
+ *   relres device [sum nsys] double  final ||S^H (b - S u)|| / ||S^H b||
+ *   status device [sum nsys] int32   WRI_SYS_*
+ * Systems are numbered group by group.  On return the stopping decision has been
+ * taken; the results are ordered on `stream`. */
+WRI_API int wri_solve_batch(const wri_group* groups, int ngroups, const wri_solve_opts* opts, int32_t* iters,
+                    double* relres, int32_t* status, void* workspace, size_t ws_bytes,
+                    wri_stream_t stream);
+
+/* Bytes of device workspace wri_source_estimate and wri_gradient need (the device
+ * copy of the geometry); wri_workspace_size is always at least this much. */
+WRI_API size_t wri_aux_workspace_size(const wri_group* groups, int ngroups);
+
+/* Source-weight estimate a_i = e_i^H A u_i = (A u_i)[src_i] (Eq. SimpObj, second
+ * block row), for every system of every group, from the wavefields in groups[g].u.
+ * alpha_out: device [2 * sum nsys] complex128.  workspace: >= wri_aux_workspace_size. */
+WRI_API int wri_source_estimate(const wri_group* groups, int ngroups, int dtype, double* alpha_out,
+                        void* workspace, size_t ws_bytes, wri_stream_t stream);
+
+/* Gradient and objective of Eqs. VarG2 / VarObj2 accumulated over every system:
+ *   grad[g][k] += sum_i omega^2 Re( conj(w_k u_ik) (A u_i - a_i e_i)_k )
+ *   f[0]       += sum_i 1/2 ||A u_i - a_i e_i||^2 + 1/2 lambda^2 ||P_i u_i - d_i||^2
+ * a_i = alpha_in (device [2 * sum nsys] complex128), normally wri_source_estimate's output
+ * in source-free mode or the known weights otherwise.  grad: host array of ngroups
+ * device pointers, each [n_g] double; f: device [1] double.  The caller zeroes them.
+ * Systems of a group are summed in a fixed order per node; f is summed with FP64
+ * atomics (last-bit order dependence).  workspace: >= wri_aux_workspace_size. */
+WRI_API int wri_gradient(const wri_group* groups, int ngroups, int dtype, const double* alpha_in,
+                 double* const* grad, double* f, void* workspace, size_t ws_bytes,
+                 wri_stream_t stream);
+
+/* Number of built tile configurations and the thread-block shape of one of them. */
+WRI_API int wri_tile_count(void);
+WRI_API int wri_tile_shape(int tile, int* bx, int* by);
+
+/* Static description of an error code. */
+WRI_API const char* wri_strerror(int code);
+
+/* Library version string. */
+WRI_API const char* wri_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WRI_H */

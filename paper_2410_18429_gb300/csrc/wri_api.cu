@@ -1,0 +1,800 @@
+// C ABI of libwri (include/wri.h): argument validation, workspace layout, launch
+// sequencing, the CUDA-graph-captured CG iteration loop, FP64 iterative refinement
+// and the unfused baseline path.  All arithmetic runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/wri.h"
+#include "wri_launch.h"
+
+using namespace wri;
+
+namespace {
+
+constexpr int kRefSMs = 152;  // SMs of a GB300; sets the z-split of small batches
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int by_of_tile(int tile) {
+  switch (tile) {
+    case 1: return 4;
+    case 3: return 16;
+    default: return 8;
+  }
+}
+
+#define WRI_CK(call)                          \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return WRI_ECUDA;  \
+  } while (0)
+
+bool grid_valid(const wri_grid* g) {
+  if (!g) return false;
+  if (g->nx < 3 || g->ny < 3 || g->nz < 3) return false;
+  if (g->npml < 0 || 2 * g->npml >= g->nx || 2 * g->npml >= g->ny || 2 * g->npml >= g->nz) return false;
+  if (!(g->h > 0) || !std::isfinite(g->h) || !(g->omega > 0) || !std::isfinite(g->omega)) return false;
+  if (g->npml > 0) {
+    if (!(g->pml_R > 0 && g->pml_R < 1)) return false;
+    if (!(g->v_max > 0) || !std::isfinite(g->v_max)) return false;
+  }
+  const long long n = (long long)g->nx * g->ny * g->nz;
+  return n > 0 && n < (1LL << 40);
+}
+
+long long grid_n(const wri_grid& g) { return (long long)g.nx * g.ny * g.nz; }
+
+AxisPml axis(int n, const wri_grid& g) {
+  AxisPml a;
+  a.n = n;
+  a.npml = g.npml;
+  a.h = g.h;
+  a.inv_omega = 1.0 / g.omega;
+  if (g.npml > 0) {
+    const double L = g.npml * g.h;
+    a.smax = 3.0 * g.v_max * std::log(1.0 / g.pml_R) / (2.0 * L);
+    a.invL = 1.0 / L;
+  } else {
+    a.smax = 0.0;
+    a.invL = 0.0;
+  }
+  return a;
+}
+
+void fill_geom(GroupDev& G, const wri_grid& g) {
+  G.nx = g.nx;
+  G.ny = g.ny;
+  G.nz = g.nz;
+  G.npml = g.npml;
+  G.h = g.h;
+  G.omega = g.omega;
+  G.ax = axis(g.nx, g);
+  G.ay = axis(g.ny, g);
+  G.az = axis(g.nz, g);
+  G.n = grid_n(g);
+}
+
+// tiles_x, tiles_y, zsplit, zc of a grid for a given batch size
+void decompose(const wri_grid& g, int by, int zs_req, GroupDev& G) {
+  G.tiles_x = (g.nx + WRI_TX - 1) / WRI_TX;
+  G.tiles_y = (g.ny + by - 1) / by;
+  int zs = std::max(1, std::min(zs_req, std::max(1, g.nz / 4)));
+  G.zc = (g.nz + zs - 1) / zs;
+  G.zsplit = (g.nz + G.zc - 1) / G.zc;
+  G.ntiles = G.tiles_x * G.tiles_y * G.zsplit;
+}
+
+int auto_zsplit(long long xy_items) {
+  int zs = 1;
+  while (xy_items * zs < 8LL * kRefSMs && zs < 16) zs *= 2;
+  return zs;
+}
+
+int validate_groups(const wri_group* groups, int ngroups, bool need_data) {
+  if (!groups || ngroups < 1 || ngroups > WRI_MAXG) return WRI_EINVAL;
+  long long nsys_total = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const wri_group& G = groups[gi];
+    if (!grid_valid(&G.grid)) return WRI_EINVAL;
+    if (!G.m || !G.u || G.nsys < 1 || !G.src_idx || !G.rec_off || !G.rec_idx) return WRI_EINVAL;
+    if (!(G.lambda > 0) || !std::isfinite(G.lambda)) return WRI_EINVAL;
+    const long long n = grid_n(G.grid);
+    if (G.rec_off[0] != 0) return WRI_EINVAL;
+    for (int s = 0; s < G.nsys; ++s) {
+      if (G.src_idx[s] < 0 || G.src_idx[s] >= n) return WRI_EINVAL;
+      const int a = G.rec_off[s], b = G.rec_off[s + 1];
+      if (b < a) return WRI_EINVAL;
+      std::vector<int> r(G.rec_idx + a, G.rec_idx + b);
+      for (int v : r)
+        if (v < 0 || v >= n) return WRI_EINVAL;
+      std::sort(r.begin(), r.end());
+      if (std::adjacent_find(r.begin(), r.end()) != r.end()) return WRI_EINVAL;
+    }
+    if (need_data && G.rec_off[G.nsys] > 0 && !G.d) return WRI_EINVAL;
+    nsys_total += G.nsys;
+  }
+  if (nsys_total > (1 << 24)) return WRI_EINVAL;
+  return WRI_OK;
+}
+
+struct Plan {
+  int ngroups = 0, nsys_total = 0, nnz_total = 0, dtype = 0, ir = 0, by = 8;
+  int vbytes = 8;   // bytes of one complex of the iteration vectors
+  int rlbytes = 8;  // bytes of one complex of lamd / r2
+  long long nitems = 0;
+  long long nparts = 0;
+  size_t off_sys = 0, off_rec = 0, off_part = 0, off_rem = 0, off_lamd = 0, off_r2 = 0;
+  size_t aux_total = 0, total = 0;
+  GroupDev g[WRI_MAXG];
+  size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][2], v_s[WRI_MAXG], v_t1[WRI_MAXG];
+  size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG];
+  std::vector<int> rec_base;  // first receiver entry of every group
+};
+
+void plan_aux(const wri_group* groups, int ngroups, Plan& P) {
+  P.ngroups = ngroups;
+  P.nsys_total = 0;
+  P.nnz_total = 0;
+  P.rec_base.assign(ngroups, 0);
+  for (int gi = 0; gi < ngroups; ++gi) {
+    P.rec_base[gi] = P.nnz_total;
+    P.nsys_total += groups[gi].nsys;
+    P.nnz_total += groups[gi].rec_off[groups[gi].nsys];
+  }
+  size_t off = 0;
+  P.off_sys = off;
+  off += align_up(sizeof(SysDev) * (size_t)P.nsys_total);
+  P.off_rec = off;
+  off += align_up(sizeof(int) * (size_t)std::max(P.nnz_total, 1));
+  P.aux_total = off;
+  P.total = off;
+}
+
+void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, Plan& P) {
+  plan_aux(groups, ngroups, P);
+  P.dtype = o->dtype;
+  P.ir = (o->dtype == WRI_C64 && o->max_refine > 0) ? 1 : 0;
+  P.by = by_of_tile(o->tile);
+  P.vbytes = (o->dtype == WRI_C128) ? 16 : 8;
+  P.rlbytes = (o->dtype == WRI_C128 || P.ir) ? 16 : 8;
+  long long xy_items = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const wri_grid& g = groups[gi].grid;
+    xy_items += (long long)groups[gi].nsys * ((g.nx + WRI_TX - 1) / WRI_TX) * ((g.ny + P.by - 1) / P.by);
+  }
+  const int zs = o->zsplit > 0 ? o->zsplit : auto_zsplit(o->plain ? xy_items / std::max(1, P.nsys_total) : xy_items);
+  long long item = 0, parts = 0;
+  int sys0 = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    GroupDev& G = P.g[gi];
+    std::memset(&G, 0, sizeof(G));
+    fill_geom(G, groups[gi].grid);
+    decompose(groups[gi].grid, P.by, zs, G);
+    G.nsys = groups[gi].nsys;
+    G.sys0 = sys0;
+    G.item0 = item;
+    G.nitems = (long long)G.ntiles * G.nsys;
+    item += G.nitems;
+    parts += G.nitems;
+    sys0 += G.nsys;
+  }
+  P.nitems = item;
+  P.nparts = parts;
+  size_t off = P.total;
+  P.off_part = off;
+  off += align_up(sizeof(double) * (size_t)std::max<long long>(parts, 4096));
+  P.off_rem = off;
+  off += kAlign;
+  P.off_lamd = off;
+  off += align_up((size_t)P.rlbytes * std::max(P.nnz_total, 1));
+  P.off_r2 = off;
+  off += align_up((size_t)P.rlbytes * std::max(P.nnz_total, 1));
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const size_t vb = align_up((size_t)P.vbytes * (size_t)P.g[gi].nsys * (size_t)P.g[gi].n);
+    P.v_r1[gi][0] = off; off += vb;
+    P.v_r1[gi][1] = off; off += vb;
+    P.v_p[gi][0] = off; off += vb;
+    P.v_p[gi][1] = off; off += vb;
+    P.v_s[gi] = off; off += vb;
+    P.v_t1[gi] = off; off += vb;
+    P.v_x32[gi] = P.v_x64[gi] = P.v_r64[gi] = 0;
+    if (P.ir) {
+      const size_t nn = (size_t)P.g[gi].nsys * (size_t)P.g[gi].n;
+      P.v_x32[gi] = off; off += align_up(8 * nn);
+      P.v_x64[gi] = off; off += align_up(16 * nn);
+      P.v_r64[gi] = off; off += align_up(16 * nn);
+    }
+  }
+  P.total = off;
+}
+
+int validate_opts(const wri_solve_opts* o) {
+  if (!o) return WRI_EINVAL;
+  if (o->dtype != WRI_C64 && o->dtype != WRI_C128) return WRI_EINVAL;
+  if (!(o->tol >= 0) || !std::isfinite(o->tol) || o->max_iter < 1) return WRI_EINVAL;
+  if (o->max_refine < 0 || o->poll_every < 0 || o->tile < 0 || o->tile > 3 || o->zsplit < 0) return WRI_EINVAL;
+  if (o->max_refine > 0) {
+    if (o->dtype != WRI_C64) return WRI_ENOTSUP;
+    if (!(o->refine_tol >= 0) || !(o->inner_tol > 0 && o->inner_tol < 1)) return WRI_EINVAL;
+    if (o->plain) return WRI_ENOTSUP;
+  }
+  return WRI_OK;
+}
+
+// Host copies of the per-system descriptors and the batch-wide receiver list.
+void build_sys(const wri_group* groups, int ngroups, const Plan& P, std::vector<SysDev>& sys,
+               std::vector<int>& rec) {
+  sys.assign(P.nsys_total, SysDev());
+  rec.clear();
+  rec.reserve(std::max(P.nnz_total, 1));
+  int s = 0;
+  long long part = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const wri_group& G = groups[gi];
+    for (int l = 0; l < G.nsys; ++l, ++s) {
+      SysDev& d = sys[s];
+      std::memset(&d, 0, sizeof(d));
+      d.group = gi;
+      d.local = l;
+      d.src = G.src_idx[l];
+      d.rec_begin = (int)rec.size();
+      for (int k = G.rec_off[l]; k < G.rec_off[l + 1]; ++k) rec.push_back(G.rec_idx[k]);
+      d.rec_end = (int)rec.size();
+      d.part_off = (int)part;
+      part += P.g[gi].ntiles;
+      d.state = ST_DONE;
+      d.status = WRI_SYS_OK;
+    }
+  }
+  if (rec.empty()) rec.push_back(0);
+}
+
+struct DevCtx {
+  cudaStream_t cap = nullptr;
+  int* pinned = nullptr;
+  double* pinned_d = nullptr;
+  struct Entry {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Entry> graphs;
+};
+std::mutex g_mu;
+DevCtx g_ctx[64];
+
+DevCtx* ctx() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  DevCtx* c = &g_ctx[dev];
+  if (!c->cap) {
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaHostAlloc((void**)&c->pinned, 64, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    c->pinned_d = (double*)(c->pinned + 4);
+  }
+  return c;
+}
+
+cudaError_t march(int rbytes, int obytes, int mode, bool conj, int by, const Batch& b, cudaStream_t st) {
+  if (b.nitems <= 0) return cudaSuccess;
+  if (rbytes == 4) return launch_march_f32(mode, conj, by, b, 0, st);
+  if (obytes == 8) return launch_march_f64(mode, conj, by, b, 0, st);
+  return launch_march_f64_to_f32(mode, by, b, 0, st);
+}
+
+// Base batch for the solver: geometry, workspace pointers, per-group vector views.
+Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_view) {
+  Batch b;
+  std::memset(&b, 0, sizeof(b));
+  b.ngroups = P.ngroups;
+  b.bx = WRI_TX;
+  b.by = P.by;
+  b.nitems = P.nitems;
+  b.sys = (SysDev*)(ws + P.off_sys);
+  b.partial = (double*)(ws + P.off_part);
+  b.rec_idx = (const int*)(ws + P.off_rec);
+  b.r2 = ws + P.off_r2;
+  b.lamd = ws + P.off_lamd;
+  b.remaining = (int*)(ws + P.off_rem);
+  for (int gi = 0; gi < P.ngroups; ++gi) {
+    GroupDev G = P.g[gi];
+    const wri_group& U = groups[gi];
+    G.lambda = U.lambda;
+    G.masked = U.alpha ? 0 : 1;
+    G.m = U.m;
+    G.m_double = P.dtype == WRI_C128 ? 1 : 0;
+    G.d = U.d;
+    G.alpha = U.alpha;
+    G.r1[0] = ws + P.v_r1[gi][0];
+    G.r1[1] = ws + P.v_r1[gi][1];
+    G.p[0] = ws + P.v_p[gi][0];
+    G.p[1] = ws + P.v_p[gi][1];
+    G.s = ws + P.v_s[gi];
+    G.t1 = ws + P.v_t1[gi];
+    G.x = (P.ir && inner_view) ? (void*)(ws + P.v_x32[gi]) : U.u;
+    G.x64 = P.ir ? ws + P.v_x64[gi] : nullptr;
+    G.r64 = P.ir ? ws + P.v_r64[gi] : nullptr;
+    b.g[gi] = G;
+  }
+  return b;
+}
+
+int poll_default(const Plan& P) {
+  double bytes = 0;
+  for (int gi = 0; gi < P.ngroups; ++gi) bytes += 80.0 * P.g[gi].nsys * (double)P.g[gi].n;
+  const double t_iter = bytes / 6.0e12 + 6e-6;  // seconds per CG iteration of the batch (estimate)
+  int k = (int)std::ceil(300e-6 / t_iter);
+  return std::max(2, std::min(k, 256));
+}
+
+// Runs CG iterations (phase 1 + phase 2) in CUDA-graph batches of K until no system remains.
+int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, int max_iter, cudaStream_t st) {
+  DevCtx* c = ctx();
+  if (!c) return WRI_ECUDA;
+  const int rb = P.ir ? 4 : P.vbytes / 2;
+  // graph lookup / capture
+  std::vector<unsigned char> key(sizeof(Batch) * 2 + 4 * sizeof(int));
+  std::memcpy(key.data(), &b1, sizeof(Batch));
+  std::memcpy(key.data() + sizeof(Batch), &b2, sizeof(Batch));
+  const int extra[4] = {mode2, K, P.by, rb};
+  std::memcpy(key.data() + 2 * sizeof(Batch), extra, sizeof(extra));
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& e : c->graphs)
+      if (e.key == key) exec = e.exec;
+    if (!exec) {
+      cudaGraph_t graph = nullptr;
+      WRI_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+      cudaError_t err = cudaSuccess;
+      for (int k = 0; k < K && err == cudaSuccess; ++k) {
+        err = march(rb, rb, M_P1, false, P.by, b1, c->cap);
+        if (err == cudaSuccess) err = march(rb, rb, mode2, true, P.by, b2, c->cap);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+      if (err != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return WRI_ECUDA;
+      }
+      e2 = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e2 != cudaSuccess) return WRI_ECUDA;
+      if (c->graphs.size() >= 8) {
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+      }
+      DevCtx::Entry e;
+      e.key = key;
+      e.exec = exec;
+      c->graphs.push_back(e);
+    }
+  }
+  long long launched = 0;
+  for (;;) {
+    WRI_CK(cudaGraphLaunch(exec, st));
+    launched += K;
+    WRI_CK(cudaMemcpyAsync(c->pinned, b1.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WRI_CK(cudaStreamSynchronize(st));
+    if (*c->pinned <= 0) break;
+    if (launched > (long long)max_iter + 2 * K + 2) return WRI_ECUDA;  // a system failed to stop
+  }
+  return WRI_OK;
+}
+
+int upload(const wri_group* groups, int ngroups, const Plan& P, char* ws, cudaStream_t st) {
+  std::vector<SysDev> sys;
+  std::vector<int> rec;
+  build_sys(groups, ngroups, P, sys, rec);
+  WRI_CK(cudaMemcpyAsync(ws + P.off_sys, sys.data(), sizeof(SysDev) * sys.size(), cudaMemcpyHostToDevice, st));
+  WRI_CK(cudaMemcpyAsync(ws + P.off_rec, rec.data(), sizeof(int) * rec.size(), cudaMemcpyHostToDevice, st));
+  return WRI_OK;
+}
+
+int check_ws(const Plan& P, const void* ws, size_t bytes) {
+  if (!ws || ((uintptr_t)ws % kAlign) != 0 || bytes < P.total) return WRI_EWORKSPACE;
+  return WRI_OK;
+}
+
+// ---------------------------------------------------------------- fused, batched solve
+int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, const Plan& P, char* ws,
+                cudaStream_t st) {
+  Batch b = solver_batch(groups, P, ws, false);
+  b.max_iter = o->max_iter;
+  b.tol = o->tol;
+  const int vb = P.vbytes / 2;
+  WRI_CK(launch_setup_rhs(o->dtype == WRI_C128 ? 8 : 4, vb, b, P.nsys_total, st));
+  WRI_CK(cudaMemsetAsync(b.remaining, 0, sizeof(int), st));
+  if (o->warm_start) {
+    Batch r = b;
+    r.flavor = SH_REF;
+    WRI_CK(march(vb, vb, M_SH, true, P.by, r, st));
+    r.flavor = 0;
+    WRI_CK(march(vb, vb, M_RES, false, P.by, r, st));
+    r.flavor = SH_WARM;
+    WRI_CK(march(vb, vb, M_SH, true, P.by, r, st));
+  } else {
+    Batch r = b;
+    r.flavor = SH_INIT;
+    WRI_CK(march(vb, vb, M_SH, true, P.by, r, st));
+  }
+  Batch b1 = b, b2 = b;
+  b1.flavor = b2.flavor = 0;
+  const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
+  return run_loop(P, b1, b2, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st);
+}
+
+// ---------------------------------------------------------------- FP64 iterative refinement
+int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o, const Plan& P, char* ws,
+                  cudaStream_t st) {
+  DevCtx* c = ctx();
+  if (!c) return WRI_ECUDA;
+  Batch outer = solver_batch(groups, P, ws, false);  // FP64 views: x = x64, r1[0] = r64
+  for (int gi = 0; gi < P.ngroups; ++gi) {
+    outer.g[gi].x = outer.g[gi].x64;
+    outer.g[gi].r1[0] = outer.g[gi].r64;
+  }
+  outer.max_iter = o->max_iter;
+  outer.tol = o->tol;
+  outer.refine_tol = o->refine_tol;
+  outer.inner_tol = o->inner_tol;
+  outer.max_refine = o->max_refine;
+  outer.warm = o->warm_start ? 1 : 0;
+  Batch inner = solver_batch(groups, P, ws, true);  // FP32 views: x = x32
+  inner.max_iter = o->max_iter;
+  inner.cgnr = 1;
+  // lambda d in FP64, x64 = warm ? u : 0, x32 = 0
+  WRI_CK(launch_setup_rhs(4, 8, outer, P.nsys_total, st));
+  {
+    Batch z = inner;
+    for (int gi = 0; gi < P.ngroups; ++gi) z.g[gi].d = groups[gi].u;
+    WRI_CK(launch_ir_init(z, o->warm_start ? 1 : 0, st));
+  }
+  if (o->warm_start) {  // ||S^H b|| with the FP64 stencil
+    Batch r = outer;
+    r.flavor = SH_REF;
+    WRI_CK(launch_march_f64_to_f32(M_SH, P.by, r, 0, st));
+  }
+  const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
+  for (int outer_k = 0;; ++outer_k) {
+    WRI_CK(cudaMemsetAsync(outer.remaining, 0, sizeof(int), st));
+    Batch r = outer;
+    r.outer = outer_k;
+    r.flavor = SH_REFINE;
+    WRI_CK(march(8, 8, M_RES, false, P.by, r, st));
+    WRI_CK(launch_march_f64_to_f32(M_SH, P.by, r, 0, st));
+    WRI_CK(cudaMemcpyAsync(c->pinned, outer.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WRI_CK(cudaStreamSynchronize(st));
+    if (*c->pinned <= 0) break;
+    const int rc = run_loop(P, inner, inner, M_P2N, std::min(K, o->max_iter + 1), o->max_iter, st);
+    if (rc != WRI_OK) return rc;
+    Batch a = inner;
+    for (int gi = 0; gi < P.ngroups; ++gi) a.g[gi].x64 = outer.g[gi].x64;
+    WRI_CK(launch_ir_accum(a, 0, st));
+    if (outer_k > o->max_refine + 1) return WRI_ECUDA;
+  }
+  Batch f = inner;
+  for (int gi = 0; gi < P.ngroups; ++gi) f.g[gi].t1 = groups[gi].u;
+  WRI_CK(launch_ir_accum(f, 1, st));
+  return WRI_OK;
+}
+
+// ---------------------------------------------------------------- unfused baseline
+// One system at a time: separate stencil, BLAS-1 and dot kernels, every scalar read
+// back by the host.  Iterates and stopping rule are those of the fused path.
+int solve_plain(const wri_group* groups, int ngroups, const wri_solve_opts* o, const Plan& P, char* ws,
+                int32_t* iters, double* relres, int32_t* status, cudaStream_t st) {
+  DevCtx* c = ctx();
+  if (!c) return WRI_ECUDA;
+  const int rb = P.vbytes / 2;
+  const size_t cb = P.vbytes;
+  double* part = (double*)(ws + P.off_part);
+  double* dres = part + 2048;  // two device scalars after the dot partials
+  std::vector<SysDev> sys;
+  std::vector<int> rec;
+  build_sys(groups, ngroups, P, sys, rec);
+  const int* rec_dev = (const int*)(ws + P.off_rec);
+  int sidx = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const wri_group& U = groups[gi];
+    GroupDev G1 = P.g[gi];
+    G1.lambda = U.lambda;
+    G1.masked = U.alpha ? 0 : 1;
+    G1.m = U.m;
+    G1.m_double = P.dtype == WRI_C128 ? 1 : 0;
+    decompose(U.grid, P.by, o->zsplit > 0 ? o->zsplit : auto_zsplit((long long)G1.tiles_x * G1.tiles_y), G1);
+    G1.nsys = 1;
+    G1.sys0 = 0;
+    G1.item0 = 0;
+    G1.nitems = G1.ntiles;
+    const long long n = G1.n;
+    for (int l = 0; l < U.nsys; ++l, ++sidx) {
+      const SysDev& sd = sys[sidx];
+      const int nr = sd.rec_end - sd.rec_begin;
+      char* r1 = ws + P.v_r1[gi][0] + (size_t)l * n * cb;
+      char* p = ws + P.v_p[gi][0] + (size_t)l * n * cb;
+      char* s = ws + P.v_s[gi] + (size_t)l * n * cb;
+      char* t1 = ws + P.v_t1[gi] + (size_t)l * n * cb;
+      char* x = (char*)U.u + (size_t)l * n * cb;
+      char* r2 = ws + P.off_r2 + (size_t)sd.rec_begin * cb;
+      char* t2 = ws + P.off_lamd + (size_t)sd.rec_begin * cb;
+      const char* dd = (const char*)U.d + (size_t)(sd.rec_begin - P.rec_base[gi]) * cb;
+      const int* rc = rec_dev + sd.rec_begin;
+      Batch a;
+      std::memset(&a, 0, sizeof(a));
+      a.ngroups = 1;
+      a.bx = WRI_TX;
+      a.by = P.by;
+      a.nitems = G1.nitems;
+      a.g[0] = G1;
+      auto apply = [&](const void* in, void* out, bool conj) -> cudaError_t {
+        Batch q = a;
+        q.g[0].x = const_cast<void*>(in);
+        q.g[0].s = out;
+        return march(rb, rb, M_APPLY, conj, P.by, q, st);
+      };
+      auto dot2 = [&](const void* v1, long long n1, const void* v2, long long n2, double& out) -> int {
+        WRI_CK(plain_dot(rb, v1, n1, part, dres, st));
+        if (v2 && n2 > 0) WRI_CK(plain_dot(rb, v2, n2, part, dres + 1, st));
+        WRI_CK(cudaMemcpyAsync(c->pinned_d, dres, sizeof(double) * ((v2 && n2 > 0) ? 2 : 1),
+                               cudaMemcpyDeviceToHost, st));
+        WRI_CK(cudaStreamSynchronize(st));
+        out = c->pinned_d[0] + ((v2 && n2 > 0) ? c->pinned_d[1] : 0.0);
+        return WRI_OK;
+      };
+      // b1 = alpha e (known weight) or 0; the weight lives on the device
+      double ar = 0.0, ai = 0.0;
+      if (U.alpha) {
+        WRI_CK(cudaMemcpyAsync(c->pinned_d, U.alpha + 2 * l, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        WRI_CK(cudaStreamSynchronize(st));
+        ar = c->pinned_d[0];
+        ai = c->pinned_d[1];
+      }
+      WRI_CK(plain_fill(rb, r1, x, n, U.alpha ? sd.src : -1, ar, ai, st));
+      WRI_CK(plain_setr2(rb, r2, dd, nr, U.lambda, st));
+      WRI_CK(apply(r1, s, true));
+      WRI_CK(plain_scatter(rb, s, rc, r2, nr, U.lambda, st));
+      double gamma = 0.0;
+      if (dot2(s, n, nullptr, 0, gamma) != WRI_OK) return WRI_ECUDA;
+      const double ref = std::sqrt(gamma);
+      int it = 0, stat = WRI_SYS_OK;
+      double rr = gamma > 0 ? 1.0 : 0.0;
+      if (gamma > 0 && std::isfinite(gamma) && !(ref <= o->tol * ref)) {
+        WRI_CK(cudaMemcpyAsync(p, s, (size_t)n * cb, cudaMemcpyDeviceToDevice, st));
+        for (;;) {
+          WRI_CK(apply(p, t1, false));
+          WRI_CK(plain_gather_mask(rb, t2, p, rc, nr, U.lambda, t1, sd.src, U.alpha ? 0 : 1, st));
+          double delta = 0.0;
+          if (dot2(t1, n, t2, nr, delta) != WRI_OK) return WRI_ECUDA;
+          if (!(delta > 0) || !std::isfinite(delta)) {
+            stat = std::isfinite(delta) ? WRI_SYS_BREAKDOWN : WRI_SYS_NONFINITE;
+            break;
+          }
+          const double al = gamma / delta;
+          WRI_CK(plain_axpy(rb, x, p, al, n, st));
+          WRI_CK(plain_axpy(rb, r1, t1, -al, n, st));
+          WRI_CK(plain_axpy(rb, r2, t2, -al, nr, st));
+          WRI_CK(apply(r1, s, true));
+          WRI_CK(plain_scatter(rb, s, rc, r2, nr, U.lambda, st));
+          double gn = 0.0;
+          if (dot2(s, n, nullptr, 0, gn) != WRI_OK) return WRI_ECUDA;
+          ++it;
+          rr = std::sqrt(gn) / ref;
+          if (!std::isfinite(gn)) {
+            stat = WRI_SYS_NONFINITE;
+            break;
+          }
+          if (std::sqrt(gn) <= o->tol * ref) break;
+          if (it >= o->max_iter) {
+            stat = WRI_SYS_MAXITER;
+            break;
+          }
+          const double beta = gn / gamma;
+          gamma = gn;
+          WRI_CK(plain_xpby(rb, p, s, beta, n, st));
+        }
+      } else if (!std::isfinite(gamma)) {
+        stat = WRI_SYS_NONFINITE;
+      }
+      if (gamma == 0.0) rr = 0.0;
+      WRI_CK(cudaMemcpyAsync(iters + sidx, &it, sizeof(int), cudaMemcpyHostToDevice, st));
+      WRI_CK(cudaMemcpyAsync(relres + sidx, &rr, sizeof(double), cudaMemcpyHostToDevice, st));
+      WRI_CK(cudaMemcpyAsync(status + sidx, &stat, sizeof(int), cudaMemcpyHostToDevice, st));
+      WRI_CK(cudaStreamSynchronize(st));
+    }
+  }
+  return WRI_OK;
+}
+
+int apply_common(const wri_grid* grid, int dtype, const void* m, int nsys, const void* x, void* y,
+                 cudaStream_t st, bool conj) {
+  if (!grid_valid(grid) || !m || !x || !y || nsys < 1) return WRI_EINVAL;
+  if (dtype != WRI_C64 && dtype != WRI_C128) return WRI_EINVAL;
+  const long long n = grid_n(*grid);
+  const size_t vb = (dtype == WRI_C128 ? 16 : 8);
+  const char* xs = (const char*)x;
+  const char* ys = (const char*)y;
+  const size_t bytes = (size_t)n * nsys * vb;
+  if (xs < ys + bytes && ys < xs + bytes) return WRI_EINVAL;  // overlap
+  Batch b;
+  std::memset(&b, 0, sizeof(b));
+  b.ngroups = 1;
+  b.bx = WRI_TX;
+  b.by = 8;
+  GroupDev& G = b.g[0];
+  fill_geom(G, *grid);
+  decompose(*grid, 8, auto_zsplit((long long)nsys * ((grid->nx + WRI_TX - 1) / WRI_TX) * ((grid->ny + 7) / 8)), G);
+  G.nsys = nsys;
+  G.item0 = 0;
+  G.nitems = (long long)G.ntiles * nsys;
+  G.m = m;
+  G.m_double = dtype == WRI_C128 ? 1 : 0;
+  G.x = const_cast<void*>(x);
+  G.s = y;
+  b.nitems = G.nitems;
+  const int rb = dtype == WRI_C128 ? 8 : 4;
+  WRI_CK(march(rb, rb, M_APPLY, conj, 8, b, st));
+  return WRI_OK;
+}
+
+// geometry-only batch for the source estimate / gradient
+Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, int dtype) {
+  Batch b;
+  std::memset(&b, 0, sizeof(b));
+  b.ngroups = ngroups;
+  b.bx = WRI_TX;
+  b.by = 8;
+  b.sys = (SysDev*)(ws + P.off_sys);
+  b.rec_idx = (const int*)(ws + P.off_rec);
+  int sys0 = 0;
+  long long item = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    GroupDev& G = b.g[gi];
+    fill_geom(G, groups[gi].grid);
+    G.lambda = groups[gi].lambda;
+    G.nsys = groups[gi].nsys;
+    G.sys0 = sys0;
+    G.masked = groups[gi].alpha ? 0 : 1;
+    G.m = groups[gi].m;
+    G.m_double = dtype == WRI_C128 ? 1 : 0;
+    G.d = groups[gi].d;
+    G.x = groups[gi].u;
+    // gradient decomposition: one work item per tile, systems looped inside
+    G.tiles_x = (G.nx + WRI_TX - 1) / WRI_TX;
+    G.tiles_y = (G.ny + 7) / 8;
+    G.zc = grad_zc(8);
+    G.zsplit = (G.nz + G.zc - 1) / G.zc;
+    G.ntiles = G.tiles_x * G.tiles_y * G.zsplit;
+    G.item0 = item;
+    G.nitems = G.ntiles;
+    item += G.nitems;
+    sys0 += G.nsys;
+  }
+  b.nitems = item;
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wri_apply_A(const wri_grid* grid, int dtype, const void* m, int nsys, const void* x, void* y,
+                wri_stream_t stream) {
+  return apply_common(grid, dtype, m, nsys, x, y, (cudaStream_t)stream, false);
+}
+
+int wri_apply_AH(const wri_grid* grid, int dtype, const void* m, int nsys, const void* x, void* y,
+                 wri_stream_t stream) {
+  return apply_common(grid, dtype, m, nsys, x, y, (cudaStream_t)stream, true);
+}
+
+size_t wri_workspace_size(const wri_group* groups, int ngroups, const wri_solve_opts* opts) {
+  if (validate_opts(opts) != WRI_OK || validate_groups(groups, ngroups, false) != WRI_OK) return 0;
+  Plan P;
+  plan_solve(groups, ngroups, opts, P);
+  return P.total;
+}
+
+size_t wri_aux_workspace_size(const wri_group* groups, int ngroups) {
+  if (validate_groups(groups, ngroups, false) != WRI_OK) return 0;
+  Plan P;
+  plan_aux(groups, ngroups, P);
+  return P.aux_total;
+}
+
+int wri_solve_batch(const wri_group* groups, int ngroups, const wri_solve_opts* opts, int32_t* iters,
+                    double* relres, int32_t* status, void* workspace, size_t ws_bytes, wri_stream_t stream) {
+  int rc = validate_opts(opts);
+  if (rc != WRI_OK) return rc;
+  rc = validate_groups(groups, ngroups, true);
+  if (rc != WRI_OK) return rc;
+  if (!iters || !relres || !status) return WRI_EINVAL;
+  Plan P;
+  plan_solve(groups, ngroups, opts, P);
+  rc = check_ws(P, workspace, ws_bytes);
+  if (rc != WRI_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  rc = upload(groups, ngroups, P, ws, st);
+  if (rc != WRI_OK) return rc;
+  if (opts->plain) return solve_plain(groups, ngroups, opts, P, ws, iters, relres, status, st);
+  rc = P.ir ? solve_refined(groups, ngroups, opts, P, ws, st) : solve_fused(groups, ngroups, opts, P, ws, st);
+  if (rc != WRI_OK) return rc;
+  WRI_CK(launch_export((const SysDev*)(ws + P.off_sys), P.nsys_total, iters, relres, status, st));
+  return WRI_OK;
+}
+
+int wri_source_estimate(const wri_group* groups, int ngroups, int dtype, double* alpha_out, void* workspace,
+                        size_t ws_bytes, wri_stream_t stream) {
+  if (dtype != WRI_C64 && dtype != WRI_C128) return WRI_EINVAL;
+  int rc = validate_groups(groups, ngroups, false);
+  if (rc != WRI_OK) return rc;
+  if (!alpha_out) return WRI_EINVAL;
+  Plan P;
+  plan_aux(groups, ngroups, P);
+  rc = check_ws(P, workspace, ws_bytes);
+  if (rc != WRI_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  rc = upload(groups, ngroups, P, ws, st);
+  if (rc != WRI_OK) return rc;
+  Batch b = aux_batch(groups, ngroups, P, ws, dtype);
+  WRI_CK(launch_source_estimate(dtype == WRI_C128 ? 8 : 4, b, P.nsys_total, alpha_out, st));
+  return WRI_OK;
+}
+
+int wri_gradient(const wri_group* groups, int ngroups, int dtype, const double* alpha_in, double* const* grad,
+                 double* f, void* workspace, size_t ws_bytes, wri_stream_t stream) {
+  if (dtype != WRI_C64 && dtype != WRI_C128) return WRI_EINVAL;
+  int rc = validate_groups(groups, ngroups, true);
+  if (rc != WRI_OK) return rc;
+  if (!alpha_in || !grad || !f) return WRI_EINVAL;
+  for (int gi = 0; gi < ngroups; ++gi)
+    if (!grad[gi]) return WRI_EINVAL;
+  Plan P;
+  plan_aux(groups, ngroups, P);
+  rc = check_ws(P, workspace, ws_bytes);
+  if (rc != WRI_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  rc = upload(groups, ngroups, P, ws, st);
+  if (rc != WRI_OK) return rc;
+  Batch b = aux_batch(groups, ngroups, P, ws, dtype);
+  b.f = f;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    b.g[gi].alpha = alpha_in + 2 * b.g[gi].sys0;
+    b.g[gi].grad = grad[gi];
+  }
+  const int rb = dtype == WRI_C128 ? 8 : 4;
+  WRI_CK(march(rb, rb, M_GRAD, false, 8, b, st));
+  WRI_CK(launch_data_term(rb, b, P.nsys_total, st));
+  return WRI_OK;
+}
+
+int wri_tile_count(void) { return 3; }
+
+int wri_tile_shape(int tile, int* bx, int* by) {
+  if (tile < 1 || tile > 3 || !bx || !by) return WRI_EINVAL;
+  *bx = WRI_TX;
+  *by = by_of_tile(tile);
+  return WRI_OK;
+}
+
+const char* wri_strerror(int code) {
+  switch (code) {
+    case WRI_OK: return "success";
+    case WRI_EINVAL: return "invalid argument";
+    case WRI_ECUDA: return "CUDA launch or runtime error";
+    case WRI_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case WRI_ENOTSUP: return "unsupported option combination";
+  }
+  return "unknown error code";
+}
+
+const char* wri_version(void) { return "libwri 0.1 (sm_103a)"; }
+
+}  // extern "C"

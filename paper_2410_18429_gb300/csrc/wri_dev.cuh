@@ -1,0 +1,173 @@
+// Device-side definitions shared by the libwri translation units: complex helpers,
+// the stretched-coordinate factors of the absorbing layer, and the batch
+// descriptors passed to every kernel by value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define WRI_MAXG 8   // frequency groups per batched launch
+#define WRI_TX 32    // tile width in x: one warp spans one x-row of a tile
+
+namespace wri {
+
+// z-chunk of the gradient kernel (its FP64 accumulator tile lives in shared memory)
+__host__ __device__ constexpr int grad_zc(int by) { return by >= 16 ? 8 : 16; }
+
+// squared slowness at a node, in the precision of the caller's model array
+template <typename R>
+__device__ __forceinline__ R model_at(const void* m, int m_double, long long node) {
+  return m_double ? R(((const double*)m)[node]) : R(((const float*)m)[node]);
+}
+
+// ------------------------------------------------------------------ complex helpers
+template <typename R> struct CT;
+template <> struct CT<float> { typedef float2 T; };
+template <> struct CT<double> { typedef double2 T; };
+template <typename R> using cx = typename CT<R>::T;
+
+__host__ __device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+template <typename R> __host__ __device__ __forceinline__ cx<R> czero() { return mkc(R(0), R(0)); }
+
+#define WRI_COPS(T, R)                                                                              \
+  __device__ __forceinline__ T operator+(T a, T b) { return mkc(a.x + b.x, a.y + b.y); }         \
+  __device__ __forceinline__ T operator-(T a, T b) { return mkc(a.x - b.x, a.y - b.y); }         \
+  __device__ __forceinline__ T operator*(T a, T b) {                                               \
+    return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                                     \
+  }                                                                                                \
+  __device__ __forceinline__ T operator*(R s, T a) { return mkc(s * a.x, s * a.y); }             \
+  __device__ __forceinline__ T conjc(T a) { return mkc(a.x, -a.y); }                              \
+  __device__ __forceinline__ R abs2(T a) { return a.x * a.x + a.y * a.y; }                        \
+  __device__ __forceinline__ T inv(T a) {                                                          \
+    R d = R(1) / (a.x * a.x + a.y * a.y);                                                          \
+    return mkc(a.x * d, -a.y * d);                                                                 \
+  }
+WRI_COPS(float2, float)
+WRI_COPS(double2, double)
+#undef WRI_COPS
+
+__device__ __forceinline__ float2 to_c(float2 a, float) { return a; }
+__device__ __forceinline__ float2 to_c(double2 a, float) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_c(float2 a, double) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_c(double2 a, double) { return a; }
+
+// ------------------------------------------------------------------ absorbing layer (step a1)
+// s(xi) = 1 + i sigma(xi)/omega, sigma = sigma_max (xi/L)^2, xi = distance into the
+// padding from the last physical node, measured at position `pos` (node units,
+// half-integers for the half points).  CONJ returns conj(s), used by A^H.
+struct AxisPml {
+  int n, npml;
+  double h, inv_omega, smax, invL;
+};
+
+template <typename R, bool CONJ>
+__device__ __forceinline__ cx<R> stretch_at(const AxisPml& a, R pos) {
+  R xi = R(0);
+  const R lo = R(a.npml), hi = R(a.n - 1 - a.npml);
+  if (a.npml > 0) {
+    if (pos < lo) xi = (lo - pos) * R(a.h);
+    else if (pos > hi) xi = (pos - hi) * R(a.h);
+  }
+  const R q = xi * R(a.invL);
+  const R im = R(a.smax) * q * q * R(a.inv_omega);
+  return mkc(R(1), CONJ ? -im : im);
+}
+
+// ------------------------------------------------------------------ kernel modes
+enum Mode : int {
+  M_APPLY = 0,  // y = A x (or A^H x); no reduction
+  M_SH = 1,     // s = A^H r1 (+ lambda P^T r2 in the finalizer); init of a solve
+  M_RES = 2,    // r1 = b1 - Z A x, r2 = lambda (d - P x)
+  M_P1 = 3,     // p = s + beta p_old, t1 = Z A p, x += alpha_prev p_old
+  M_P2 = 4,     // r1 = r1_old - alpha t1, s = A^H r1 (CGLS)
+  M_P2N = 5,    // s = s - alpha A^H t1 (CG on the normal equations, refinement inner solve)
+  M_GRAD = 6,   // g += omega^2 Re(conj(w u)(A u - a e)), f += 1/2 |A u - a e|^2
+};
+
+// flavors of M_SH finalization
+enum ShFlavor : int {
+  SH_INIT = 0,      // cold start: F = b1 (point), writes r1 = b1, x = 0; sets snorm_b
+  SH_REF = 1,       // F = b1 (point), computes ||S^H b|| only (warm start); writes r1 = b1
+  SH_WARM = 2,      // F = r1 (from M_RES), starts the solve from the stored x
+  SH_REFINE = 3,    // F = r64 (FP64 residual), output cast to the inner s; outer test
+};
+
+// ------------------------------------------------------------------ batch descriptors
+enum SysState : int { ST_ACTIVE = 0, ST_FINISHING = 1, ST_DONE = 2 };
+
+// Per-system scalars, FP64, living in the workspace.
+struct SysDev {
+  double gamma;      // ||s||^2 of the current normal-equation residual
+  double delta;      // ||S p||^2
+  double alpha;      // step length of the current iteration
+  double beta;       // p = s + beta p
+  double snorm_b;    // ||S^H b|| (reference of the relative residual)
+  double snorm_ref;  // reference norm of the current (inner) solve
+  double relres;     // last relative residual
+  double tol;        // tolerance of the current (inner) solve, relative to snorm_ref
+  int iter;          // iterations of the current (inner) solve
+  int iter_total;    // iterations summed over refinements
+  int state;         // SysState
+  int status;        // WRI_SYS_*
+  int outer_done;    // refinement finished for this system
+  unsigned ticket;   // tile-completion counter of the running launch
+  int group;         // group index
+  int local;         // index inside the group
+  int rec_begin, rec_end;  // receiver range in the batch-wide receiver arrays
+  int part_off;      // first slot of this system in the partial-sum array
+  long long src;     // source node
+};
+
+struct GroupDev {
+  int nx, ny, nz, npml;
+  double h, omega, lambda;
+  AxisPml ax, ay, az;
+  int nsys, sys0;          // systems of the group and global index of the first
+  int tiles_x, tiles_y, zsplit, zc, ntiles;
+  long long item0, nitems;  // work items (tile x system) of the group in the batched launch
+  int masked;               // 1 = source-free (Z applied), 0 = known weight
+  long long n;              // nodes
+  const void* m;            // [n] real, float or double (m_double)
+  int m_double;             // 1 if m is double (complex128 problems), 0 if float
+  const void* d;            // [nnz] complex observed data
+  const double* alpha;      // [2*nsys] known weights or null
+  void* x;                  // [nsys][n] iterate (dtype of the stencil)
+  void* r1[2];              // [nsys][n] data-space residual, ping-pong
+  void* p[2];               // [nsys][n] search direction, ping-pong
+  void* s;                  // [nsys][n] normal-equation residual S^H r
+  void* t1;                 // [nsys][n] Z A p
+  void* x64;                // [nsys][n] double2 refinement master (or null)
+  void* r64;                // [nsys][n] double2 FP64 residual (or null)
+  double* grad;             // [n] gradient accumulator (gradient kernel only)
+};
+
+struct Batch {
+  int ngroups;
+  int bx, by;           // thread block shape (bx = WRI_TX)
+  long long nitems;     // total work items
+  SysDev* sys;
+  double* partial;      // per (system, tile) FP64 partial sums
+  const int* rec_idx;   // batch-wide receiver nodes
+  void* r2;             // batch-wide receiver residual (type of the kernel's stencil)
+  const void* lamd;     // batch-wide lambda*d (same type as r2)
+  int* remaining;       // systems not yet DONE
+  double* f;            // objective accumulator (gradient kernel only)
+  int max_iter;
+  int flavor;           // kernel-specific sub-mode
+  int cgnr;             // 1: inner solve on the normal equations (no data-space residual)
+  double tol;           // tolerance of a cold-start solve
+  double refine_tol, inner_tol;
+  int outer, max_refine, warm;
+  GroupDev g[WRI_MAXG];
+};
+
+__device__ __forceinline__ int find_group(const Batch& b, long long item) {
+  int g = 0;
+#pragma unroll 1
+  for (; g < b.ngroups - 1; ++g)
+    if (item < b.g[g + 1].item0) break;
+  return g;
+}
+
+}  // namespace wri

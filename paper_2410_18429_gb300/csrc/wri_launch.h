@@ -1,0 +1,37 @@
+// Host-side launch entry points of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wri_dev.cuh"
+
+namespace wri {
+
+// Kernel selection for the z-march: element type of the stencil (R), of its
+// output (OR), mode and conjugation.  `grid` = 0 launches one persistent wave
+// (SMs x resident CTAs, capped by the number of work items).
+cudaError_t launch_march_f32(int mode, bool conj, int by, const Batch& b, int grid, cudaStream_t st);
+cudaError_t launch_march_f64(int mode, bool conj, int by, const Batch& b, int grid, cudaStream_t st);
+cudaError_t launch_march_f64_to_f32(int mode, int by, const Batch& b, int grid, cudaStream_t st);
+
+// small kernels (wri_small.cu)
+cudaError_t launch_setup_rhs(int dtype_bytes, int rl_bytes, const Batch& b, int nsys_total, cudaStream_t st);
+cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* relres, int32_t* status,
+                          cudaStream_t st);
+cudaError_t launch_ir_init(const Batch& b, int warm, cudaStream_t st);
+cudaError_t launch_ir_accum(const Batch& b, int final_cast, cudaStream_t st);
+cudaError_t launch_source_estimate(int rbytes, const Batch& b, int nsys_total, double* alpha_out, cudaStream_t st);
+cudaError_t launch_data_term(int rbytes, const Batch& b, int nsys_total, cudaStream_t st);
+
+// unfused baseline kernels (wri_small.cu); pointers are complex of element size rbytes
+cudaError_t plain_fill(int rbytes, void* r1, void* x, long long n, long long src, double ar, double ai,
+                       cudaStream_t st);
+cudaError_t plain_setr2(int rbytes, void* r2, const void* d, int nr, double lam, cudaStream_t st);
+cudaError_t plain_scatter(int rbytes, void* s, const int* rec, const void* r2, int nr, double lam, cudaStream_t st);
+cudaError_t plain_gather_mask(int rbytes, void* t2, const void* p, const int* rec, int nr, double lam, void* t1,
+                              long long src, int masked, cudaStream_t st);
+cudaError_t plain_dot(int rbytes, const void* a, long long n, double* partial, double* out, cudaStream_t st);
+cudaError_t plain_axpy(int rbytes, void* y, const void* x, double a, long long n, cudaStream_t st);
+cudaError_t plain_xpby(int rbytes, void* p, const void* s, double beta, long long n, cudaStream_t st);
+
+}  // namespace wri

@@ -1,0 +1,120 @@
+// The z-marching stencil kernel and its fused CGLS phases.
+//
+// One CTA owns a tile of WRI_TX x BY nodes in the x-y plane and marches through a
+// z-chunk [z0, z1).  For every plane it holds the input field F of the stencil in
+// shared memory (own nodes plus a one-node halo ring, double buffered) and keeps the
+// planes k-1, k, k+1 of its own column in registers, so each input value is read
+// from memory once per tile (plus the halo ring).  The field F is formed on the fly
+// from the stored vectors (e.g. p_new = s + beta p_old), so a CG vector update and
+// the following operator application cost one pass over memory.
+//
+// Every work item is (group, tile, system); a persistent grid strides over items.
+// Per-system reductions are FP64: each tile writes one partial sum, and the CTA that
+// completes a system's last tile (atomic ticket) sums the partials in tile order,
+// adds the receiver terms and updates the system's CG scalars on the device.
+#pragma once
+
+#include "wri_dev.cuh"
+
+namespace wri {
+
+
+template <typename T>
+__device__ __forceinline__ T ldcg_c(const T* p);
+template <>
+__device__ __forceinline__ float2 ldcg_c(const float2* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ double2 ldcg_c(const double2* p) { return __ldcg(p); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum (fixed order); every thread must call it.  Result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31;
+  const int wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = (lane < NT / 32) ? red[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// Per-thread coefficients of the x and y axes for node (i, j).
+template <typename R>
+struct XYCoef {
+  cx<R> sx, sy, sxy, ixm, ixp, iym, iyp;  // ixm = 1/(s_x(i-1/2) h^2), ...
+};
+
+template <typename R, bool CONJ>
+__device__ __forceinline__ XYCoef<R> xy_coef(const GroupDev& G, int i, int j) {
+  XYCoef<R> c;
+  const R ih2 = R(1) / (R(G.h) * R(G.h));
+  c.sx = stretch_at<R, CONJ>(G.ax, R(i));
+  c.sy = stretch_at<R, CONJ>(G.ay, R(j));
+  c.sxy = c.sx * c.sy;
+  c.ixm = ih2 * inv(stretch_at<R, CONJ>(G.ax, R(i) - R(0.5)));
+  c.ixp = ih2 * inv(stretch_at<R, CONJ>(G.ax, R(i) + R(0.5)));
+  c.iym = ih2 * inv(stretch_at<R, CONJ>(G.ay, R(j) - R(0.5)));
+  c.iyp = ih2 * inv(stretch_at<R, CONJ>(G.ay, R(j) + R(0.5)));
+  return c;
+}
+
+template <typename R>
+struct ZCoef {
+  cx<R> sz, izm, izp;
+};
+
+template <typename R, bool CONJ>
+__device__ __forceinline__ ZCoef<R> z_coef(const GroupDev& G, int k) {
+  ZCoef<R> c;
+  const R ih2 = R(1) / (R(G.h) * R(G.h));
+  c.sz = stretch_at<R, CONJ>(G.az, R(k));
+  c.izm = ih2 * inv(stretch_at<R, CONJ>(G.az, R(k) - R(0.5)));
+  c.izp = ih2 * inv(stretch_at<R, CONJ>(G.az, R(k) + R(0.5)));
+  return c;
+}
+
+// First/last node index of an axis whose own stretch and both half-point stretches are 1.
+__device__ __forceinline__ void interior_range(const AxisPml& a, int& lo, int& hi) {
+  if (a.npml > 0) {
+    lo = a.npml + 1;
+    hi = a.n - 2 - a.npml;
+  } else {
+    lo = 0;
+    hi = a.n - 1;
+  }
+}
+
+// (A u) at one node with the general (stretched) coefficients.
+template <typename R, bool CONJ>
+__device__ __forceinline__ cx<R> stencil_general(const GroupDev& G, const XYCoef<R>& c, const ZCoef<R>& z,
+                                                 R om2m, cx<R> u, cx<R> uxm, cx<R> uxp, cx<R> uym,
+                                                 cx<R> uyp, cx<R> uzm, cx<R> uzp) {
+  const cx<R> syz = c.sy * z.sz;
+  const cx<R> sxz = c.sx * z.sz;
+  const cx<R> w = c.sxy * z.sz;
+  const cx<R> lx = c.ixp * (uxp - u) - c.ixm * (u - uxm);
+  const cx<R> ly = c.iyp * (uyp - u) - c.iym * (u - uym);
+  const cx<R> lz = z.izp * (uzp - u) - z.izm * (u - uzm);
+  return om2m * (w * u) + syz * lx + sxz * ly + c.sxy * lz;
+}
+
+// (A u) at one node in the interior (all stretch factors 1): omega^2 m u + Laplacian.
+template <typename R>
+__device__ __forceinline__ cx<R> stencil_interior(R ih2, R om2m, cx<R> u, cx<R> uxm, cx<R> uxp, cx<R> uym,
+                                                  cx<R> uyp, cx<R> uzm, cx<R> uzp) {
+  const cx<R> sum = (uxm + uxp) + (uym + uyp) + (uzm + uzp);
+  return mkc(om2m * u.x + ih2 * (sum.x - R(6) * u.x), om2m * u.y + ih2 * (sum.y - R(6) * u.y));
+}
+
+}  // namespace wri

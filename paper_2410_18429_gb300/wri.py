@@ -1,0 +1,254 @@
+"""ctypes binding of libwri (include/wri.h): argument marshalling only.
+
+Every numerical step runs in the CUDA kernels of ``libwri.so``.  Tensors are
+PyTorch CUDA tensors (device memory and streams); geometry (source and receiver
+node indices) is host numpy data.  If the shared library is missing this module
+raises at import: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwri.so")
+
+OK, EINVAL, ECUDA, EWORKSPACE, ENOTSUP = 0, 1, 2, 3, 4
+SYS_OK, SYS_MAXITER, SYS_BREAKDOWN, SYS_NONFINITE = 0, 1, 2, 3
+C64, C128 = 0, 1
+
+
+class WriGrid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("npml", C.c_int32),
+                ("h", C.c_double), ("omega", C.c_double), ("pml_R", C.c_double), ("v_max", C.c_double)]
+
+
+class WriGroup(C.Structure):
+    _fields_ = [("grid", WriGrid), ("m", C.c_void_p), ("nsys", C.c_int32), ("src_idx", C.c_void_p),
+                ("rec_off", C.c_void_p), ("rec_idx", C.c_void_p), ("d", C.c_void_p), ("alpha", C.c_void_p),
+                ("lam", C.c_double), ("u", C.c_void_p)]
+
+
+class WriSolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("dtype", C.c_int32),
+                ("warm_start", C.c_int32), ("max_refine", C.c_int32), ("refine_tol", C.c_double),
+                ("inner_tol", C.c_double), ("plain", C.c_int32), ("poll_every", C.c_int32),
+                ("tile", C.c_int32), ("zsplit", C.c_int32)]
+
+
+class WriError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libwri.so not built ({LIB_PATH}); run python -m paper_2410_18429_gb300.build")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, sz, dp = C.c_void_p, C.c_int, C.c_size_t, C.c_void_p
+    lib.wri_apply_A.argtypes = [C.POINTER(WriGrid), i32, vp, i32, vp, vp, vp]
+    lib.wri_apply_AH.argtypes = [C.POINTER(WriGrid), i32, vp, i32, vp, vp, vp]
+    lib.wri_workspace_size.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts)]
+    lib.wri_workspace_size.restype = sz
+    lib.wri_aux_workspace_size.argtypes = [C.POINTER(WriGroup), i32]
+    lib.wri_aux_workspace_size.restype = sz
+    lib.wri_solve_batch.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), vp, vp, vp, vp, sz, vp]
+    lib.wri_source_estimate.argtypes = [C.POINTER(WriGroup), i32, i32, dp, vp, sz, vp]
+    lib.wri_gradient.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp, sz, vp]
+    lib.wri_tile_count.argtypes = []
+    lib.wri_tile_shape.argtypes = [i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.wri_strerror.argtypes = [i32]
+    lib.wri_strerror.restype = C.c_char_p
+    lib.wri_version.restype = C.c_char_p
+    for f in ("wri_apply_A", "wri_apply_AH", "wri_solve_batch", "wri_source_estimate", "wri_gradient",
+              "wri_tile_count", "wri_tile_shape"):
+        getattr(lib, f).restype = C.c_int
+    return lib
+
+
+lib = _load()
+
+EXPORTS = ("wri_apply_A", "wri_apply_AH", "wri_workspace_size", "wri_aux_workspace_size", "wri_solve_batch",
+           "wri_source_estimate", "wri_gradient", "wri_tile_count", "wri_tile_shape", "wri_strerror",
+           "wri_version")
+
+
+def strerror(code: int) -> str:
+    return lib.wri_strerror(int(code)).decode()
+
+
+def version() -> str:
+    return lib.wri_version().decode()
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise WriError(code, what)
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class GroupSpec:
+    """One frequency group: grid, model and systems (see ``wri_group`` in include/wri.h).
+
+    m: real CUDA tensor [nz, ny, nx] (float32 for C64, float64 for C128);
+    src: int64 [nsys]; rec_off: int32 [nsys+1]; rec_idx: int32 [nnz] (host numpy);
+    d: complex CUDA tensor [nnz]; alpha: float64 CUDA tensor [nsys, 2] or None (source-free);
+    u: complex CUDA tensor [nsys, n] (initial guess with warm_start, result on return).
+    """
+
+    nx: int
+    ny: int
+    nz: int
+    npml: int
+    h: float
+    omega: float
+    v_max: float
+    m: object
+    src: np.ndarray
+    rec_off: np.ndarray
+    rec_idx: np.ndarray
+    d: object
+    lam: float
+    u: object
+    alpha: object = None
+    pml_R: float = 1e-3
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nsys(self) -> int:
+        return len(self.src)
+
+    def grid(self) -> WriGrid:
+        return WriGrid(self.nx, self.ny, self.nz, self.npml, self.h, self.omega, self.pml_R, self.v_max)
+
+
+class _Marshal:
+    """Builds the C array of wri_group and keeps the host geometry alive."""
+
+    def __init__(self, groups: Sequence[GroupSpec]):
+        self.keep = []
+        arr = (WriGroup * len(groups))()
+        for i, g in enumerate(groups):
+            src = np.ascontiguousarray(g.src, dtype=np.int64)
+            off = np.ascontiguousarray(g.rec_off, dtype=np.int32)
+            rec = np.ascontiguousarray(g.rec_idx, dtype=np.int32)
+            if len(rec) == 0:
+                rec = np.zeros(1, dtype=np.int32)
+            self.keep += [src, off, rec]
+            arr[i] = WriGroup(g.grid(), _ptr(g.m), len(src), src.ctypes.data, off.ctypes.data, rec.ctypes.data,
+                              _ptr(g.d), _ptr(g.alpha), float(g.lam), _ptr(g.u))
+        self.arr = arr
+        self.n = len(groups)
+
+
+def make_opts(tol=1e-6, max_iter=10000, dtype=C64, warm_start=False, max_refine=0, refine_tol=1e-10,
+              inner_tol=1e-3, plain=False, poll_every=0, tile=0, zsplit=0) -> WriSolveOpts:
+    return WriSolveOpts(float(tol), int(max_iter), int(dtype), int(bool(warm_start)), int(max_refine),
+                        float(refine_tol), float(inner_tol), int(bool(plain)), int(poll_every), int(tile),
+                        int(zsplit))
+
+
+def workspace_size(groups: Sequence[GroupSpec], opts: WriSolveOpts) -> int:
+    m = _Marshal(groups)
+    return int(lib.wri_workspace_size(m.arr, m.n, C.byref(opts)))
+
+
+def aux_workspace_size(groups: Sequence[GroupSpec]) -> int:
+    m = _Marshal(groups)
+    return int(lib.wri_aux_workspace_size(m.arr, m.n))
+
+
+def _workspace(nbytes: int, device, workspace=None):
+    import torch
+    if workspace is not None and workspace.numel() >= nbytes:
+        return workspace
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def apply_A(g: GroupSpec, x, adjoint: bool = False, out=None, stream=None):
+    """y = A x (or A^H x) for x [nsys, n] complex on the device."""
+    import torch
+    dtype = C128 if x.dtype == torch.complex128 else C64
+    y = torch.empty_like(x) if out is None else out
+    grid = g.grid()
+    f = lib.wri_apply_AH if adjoint else lib.wri_apply_A
+    nsys = x.shape[0] if x.dim() > 1 else 1
+    _check(f(C.byref(grid), dtype, _ptr(g.m), nsys, _ptr(x), _ptr(y), _stream(stream)), "wri_apply_A")
+    return y
+
+
+def solve(groups: Sequence[GroupSpec], opts: WriSolveOpts, workspace=None, stream=None):
+    """Solve every system; returns (iters int32, relres float64, status int32) CUDA tensors."""
+    import torch
+    m = _Marshal(groups)
+    dev = groups[0].u.device
+    nsys = sum(g.nsys for g in groups)
+    nbytes = lib.wri_workspace_size(m.arr, m.n, C.byref(opts))
+    if nbytes == 0:
+        raise WriError(EINVAL, "wri_workspace_size")
+    ws = _workspace(nbytes, dev, workspace)
+    iters = torch.zeros(nsys, dtype=torch.int32, device=dev)
+    relres = torch.zeros(nsys, dtype=torch.float64, device=dev)
+    status = torch.zeros(nsys, dtype=torch.int32, device=dev)
+    _check(lib.wri_solve_batch(m.arr, m.n, C.byref(opts), _ptr(iters), _ptr(relres), _ptr(status), _ptr(ws),
+                               ws.numel(), _stream(stream)), "wri_solve_batch")
+    return iters, relres, status
+
+
+def source_estimate(groups: Sequence[GroupSpec], dtype: int, workspace=None, stream=None):
+    """a_i = (A u_i)[src_i] for every system; returns complex128 CUDA tensor [sum nsys]."""
+    import torch
+    m = _Marshal(groups)
+    dev = groups[0].u.device
+    nsys = sum(g.nsys for g in groups)
+    ws = _workspace(lib.wri_aux_workspace_size(m.arr, m.n), dev, workspace)
+    out = torch.zeros(nsys, 2, dtype=torch.float64, device=dev)
+    _check(lib.wri_source_estimate(m.arr, m.n, dtype, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+           "wri_source_estimate")
+    return torch.view_as_complex(out)
+
+
+def gradient(groups: Sequence[GroupSpec], dtype: int, alpha, grads=None, f=None, workspace=None, stream=None):
+    """Accumulate g and f (Eqs. VarG2 / VarObj2).  alpha: complex128 [sum nsys].
+
+    Returns (list of float64 gradient tensors shaped like each group's m, f tensor [1])."""
+    import torch
+    m = _Marshal(groups)
+    dev = groups[0].u.device
+    ws = _workspace(lib.wri_aux_workspace_size(m.arr, m.n), dev, workspace)
+    if grads is None:
+        grads = [torch.zeros(g.nz, g.ny, g.nx, dtype=torch.float64, device=dev) for g in groups]
+    if f is None:
+        f = torch.zeros(1, dtype=torch.float64, device=dev)
+    a = torch.view_as_real(alpha.to(torch.complex128).contiguous())
+    gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
+    _check(lib.wri_gradient(m.arr, m.n, dtype, _ptr(a), gp, _ptr(f), _ptr(ws), ws.numel(), _stream(stream)),
+           "wri_gradient")
+    return grads, f
+
+
+def tile_shapes():
+    out = []
+    for t in range(1, lib.wri_tile_count() + 1):
+        bx, by = C.c_int(), C.c_int()
+        _check(lib.wri_tile_shape(t, C.byref(bx), C.byref(by)), "wri_tile_shape")
+        out.append((bx.value, by.value))
+    return out

@@ -1,0 +1,113 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol that
+include/wri.h declares, and rejects invalid arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def W():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2410_18429_gb300 import wri
+    return wri
+
+
+def test_exports_every_declared_symbol(W):
+    hdr = open(os.path.join(ROOT, "include", "wri.h")).read()
+    declared = set(re.findall(r"WRI_API\s+[\w\s\*]+?\b(wri_\w+)\s*\(", hdr))
+    assert declared == set(W.EXPORTS)
+    lib = C.CDLL(W.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_tiles(W):
+    assert W.strerror(0) == "success"
+    assert "invalid" in W.strerror(1)
+    assert W.strerror(99) == "unknown error code"
+    assert W.tile_shapes() == [(32, 4), (32, 8), (32, 16)]
+    assert W.version().startswith("libwri")
+
+
+class _FakeTensor:
+    """Stands in for a device tensor: only its address is read by the marshalling."""
+
+    def __init__(self, addr=0x10000):
+        self.addr = addr
+
+    def data_ptr(self):
+        return self.addr
+
+
+def _spec(W, **kw):
+    base = dict(nx=20, ny=18, nz=16, npml=3, h=10.0, omega=60.0, v_max=2000.0, m=_FakeTensor(),
+                src=np.array([1000, 1500]), rec_off=np.array([0, 3, 5]), rec_idx=np.array([10, 20, 30, 40, 50]),
+                d=_FakeTensor(), lam=0.01, u=_FakeTensor())
+    base.update(kw)
+    return W.GroupSpec(**base)
+
+
+def test_workspace_size_validation(W):
+    o = W.make_opts()
+    good = W.workspace_size([_spec(W)], o)
+    assert good > 0
+    n = 20 * 18 * 16
+    # vectors r1 x2, p x2, s, t1 for 2 systems at 8 bytes per complex
+    assert good >= 6 * 2 * n * 8
+    assert W.aux_workspace_size([_spec(W)]) < good
+    bad = [
+        _spec(W, nx=2),
+        _spec(W, npml=9),                               # 2*npml >= ny
+        _spec(W, h=0.0),
+        _spec(W, lam=-1.0),
+        _spec(W, src=np.array([1000, n])),              # source out of range
+        _spec(W, rec_idx=np.array([10, 20, 30, 40, n])),
+        _spec(W, rec_idx=np.array([10, 20, 10, 40, 50])),  # duplicate receiver in system 0
+        _spec(W, rec_off=np.array([1, 3, 5])),
+        _spec(W, rec_off=np.array([0, 4, 3])),
+        _spec(W, m=None),
+    ]
+    for s in bad:
+        assert W.workspace_size([s], o) == 0
+    assert W.workspace_size([_spec(W)], W.make_opts(dtype=7)) == 0
+    assert W.workspace_size([_spec(W)], W.make_opts(max_iter=0)) == 0
+    assert W.workspace_size([_spec(W)], W.make_opts(tol=float("nan"))) == 0
+    assert W.workspace_size([_spec(W)] * 9, o) == 0        # more groups than one launch holds
+    # refinement adds the FP64 master, the FP64 residual and the FP32 correction
+    ir = W.workspace_size([_spec(W)], W.make_opts(max_refine=3))
+    assert ir >= good + 2 * n * (8 + 16 + 16)
+    assert W.workspace_size([_spec(W)], W.make_opts(max_refine=3, dtype=W.C128)) == 0
+
+
+def test_solve_rejects_before_device_work(W):
+    o = W.make_opts()
+    m = W._Marshal([_spec(W, rec_idx=np.array([10, 20, 10, 40, 50]))])
+    rc = W.lib.wri_solve_batch(m.arr, m.n, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 30, None)
+    assert rc == W.EINVAL
+    m = W._Marshal([_spec(W)])
+    # misaligned / too small workspace
+    rc = W.lib.wri_solve_batch(m.arr, m.n, C.byref(o), 0x100, 0x200, 0x300, 0x1001, 1 << 30, None)
+    assert rc == W.EWORKSPACE
+    rc = W.lib.wri_solve_batch(m.arr, m.n, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 16, None)
+    assert rc == W.EWORKSPACE
+    rc = W.lib.wri_solve_batch(m.arr, m.n, C.byref(o), None, 0x200, 0x300, 0x1000, 1 << 30, None)
+    assert rc == W.EINVAL
+    # refinement is C64 only; the baseline path does not refine
+    o2 = W.make_opts(max_refine=2, plain=True)
+    rc = W.lib.wri_solve_batch(m.arr, m.n, C.byref(o2), 0x100, 0x200, 0x300, 0x1000, 1 << 40, None)
+    assert rc == W.ENOTSUP
+
+
+def test_apply_rejects_overlap_and_bad_grid(W):
+    g = W.WriGrid(20, 18, 16, 3, 10.0, 60.0, 1e-3, 2000.0)
+    n = 20 * 18 * 16
+    assert W.lib.wri_apply_A(C.byref(g), 0, 0x1000, 1, 0x100000, 0x100000 + 8 * (n - 1), None) == W.EINVAL
+    g2 = W.WriGrid(20, 18, 16, 3, 10.0, 60.0, 2.0, 2000.0)   # pml_R outside (0, 1)
+    assert W.lib.wri_apply_A(C.byref(g2), 0, 0x1000, 1, 0x100000, 0x900000, None) == W.EINVAL
+    assert W.lib.wri_apply_AH(C.byref(g), 5, 0x1000, 1, 0x100000, 0x900000, None) == W.EINVAL
