@@ -55,6 +55,7 @@ typedef struct CUstream_st* wri_stream_t; /* identical to cudaStream_t */
 #define WRI_ECUDA 2       /* a CUDA launch or runtime call failed */
 #define WRI_EWORKSPACE 3  /* workspace pointer null, misaligned (256 B) or too small */
 #define WRI_ENOTSUP 4     /* valid but unsupported combination of options */
+#define WRI_ESCRATCH 5    /* problem larger than the static scratch of wri_gradient_noalloc */
 
 /* per-system status written by wri_solve_batch */
 #define WRI_SYS_OK 0         /* relative normal-equation residual <= tol */
@@ -156,6 +157,26 @@ WRI_API int wri_source_estimate(const wri_group* groups, int ngroups, int dtype,
 WRI_API int wri_gradient(const wri_group* groups, int ngroups, int dtype, const double* alpha_in,
                  double* const* grad, double* f, void* workspace, size_t ws_bytes,
                  wri_stream_t stream);
+
+/* Allocation-free variant of wri_gradient (the paper has no counterpart: this is an
+ * interface for callers that cannot call cudaMalloc, e.g. code whose device memory is
+ * owned by another allocator such as a framework's caching pool that has reserved the
+ * GPU, or a latency-critical loop that must not pay cudaMalloc's implicit device
+ * synchronisation).  Same arguments and results as wri_gradient, without the
+ * workspace: the device copy of the geometry goes to a static device array of
+ * WRI_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until exit.
+ *   - Problems whose geometry needs more than that (wri_aux_workspace_size) are
+ *     rejected with WRI_ESCRATCH before any work is enqueued.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ *   - Every call reuses the same array and overwrites what it needs; two calls whose
+ *     work overlaps on the GPU (different streams, or different host threads) race on
+ *     it and must be serialised by the caller.
+ *   - The call itself allocates no device memory (no cudaMalloc / cudaFree, no
+ *     allocating library routine); grad and f are the caller's. */
+#define WRI_NOALLOC_SCRATCH_BYTES (4u << 20)
+WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype, const double* alpha_in,
+                                 double* const* grad, double* f, wri_stream_t stream);
 
 /* Number of built tile configurations and the thread-block shape of one of them. */
 WRI_API int wri_tile_count(void);

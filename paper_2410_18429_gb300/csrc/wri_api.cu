@@ -678,9 +678,60 @@ Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, i
   return b;
 }
 
+// ---------------------------------------------------------------- allocation-free gradient
+// Scratch of wri_gradient_noalloc: the device copy of the geometry (per-system
+// descriptors and receiver list).  Host code must not hand the symbol itself to a
+// kernel; it looks up the device address once per device (noalloc_scratch).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WRI_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64];
+
+int noalloc_scratch(char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WRI_ECUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return WRI_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (char*)g_noalloc_ptr[dev];
+  return WRI_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype, const double* alpha_in,
+                         double* const* grad, double* f, wri_stream_t stream) {
+  if (dtype != WRI_C64 && dtype != WRI_C128) return WRI_EINVAL;
+  int rc = validate_groups(groups, ngroups, true);
+  if (rc != WRI_OK) return rc;
+  if (!alpha_in || !grad || !f) return WRI_EINVAL;
+  for (int gi = 0; gi < ngroups; ++gi)
+    if (!grad[gi]) return WRI_EINVAL;
+  Plan P;
+  plan_aux(groups, ngroups, P);
+  if (P.aux_total > (size_t)WRI_NOALLOC_SCRATCH_BYTES) return WRI_ESCRATCH;
+  char* ws = nullptr;
+  rc = noalloc_scratch(&ws);
+  if (rc != WRI_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = upload(groups, ngroups, P, ws, st);  // overwrites every byte the kernels read
+  if (rc != WRI_OK) return rc;
+  Batch b = aux_batch(groups, ngroups, P, ws, dtype);
+  b.f = f;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    b.g[gi].alpha = alpha_in + 2 * b.g[gi].sys0;
+    b.g[gi].grad = grad[gi];
+  }
+  const int rb = dtype == WRI_C128 ? 8 : 4;
+  WRI_CK(march(rb, rb, M_GRAD, false, 8, b, st));
+  WRI_CK(launch_data_term(rb, b, P.nsys_total, st));
+  return WRI_OK;
+}
+
 
 int wri_apply_A(const wri_grid* grid, int dtype, const void* m, int nsys, const void* x, void* y,
                 wri_stream_t stream) {
@@ -791,6 +842,7 @@ const char* wri_strerror(int code) {
     case WRI_ECUDA: return "CUDA launch or runtime error";
     case WRI_EWORKSPACE: return "workspace missing, misaligned or too small";
     case WRI_ENOTSUP: return "unsupported option combination";
+    case WRI_ESCRATCH: return "problem exceeds the static scratch of the allocation-free entry point";
   }
   return "unknown error code";
 }

@@ -17,7 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libwri.so")
 
-OK, EINVAL, ECUDA, EWORKSPACE, ENOTSUP = 0, 1, 2, 3, 4
+OK, EINVAL, ECUDA, EWORKSPACE, ENOTSUP, ESCRATCH = 0, 1, 2, 3, 4, 5
+NOALLOC_SCRATCH_BYTES = 4 << 20
 SYS_OK, SYS_MAXITER, SYS_BREAKDOWN, SYS_NONFINITE = 0, 1, 2, 3
 C64, C128 = 0, 1
 
@@ -60,13 +61,14 @@ def _load():
     lib.wri_solve_batch.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), vp, vp, vp, vp, sz, vp]
     lib.wri_source_estimate.argtypes = [C.POINTER(WriGroup), i32, i32, dp, vp, sz, vp]
     lib.wri_gradient.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp, sz, vp]
+    lib.wri_gradient_noalloc.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp]
     lib.wri_tile_count.argtypes = []
     lib.wri_tile_shape.argtypes = [i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.wri_strerror.argtypes = [i32]
     lib.wri_strerror.restype = C.c_char_p
     lib.wri_version.restype = C.c_char_p
     for f in ("wri_apply_A", "wri_apply_AH", "wri_solve_batch", "wri_source_estimate", "wri_gradient",
-              "wri_tile_count", "wri_tile_shape"):
+              "wri_gradient_noalloc", "wri_tile_count", "wri_tile_shape"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -74,8 +76,8 @@ def _load():
 lib = _load()
 
 EXPORTS = ("wri_apply_A", "wri_apply_AH", "wri_workspace_size", "wri_aux_workspace_size", "wri_solve_batch",
-           "wri_source_estimate", "wri_gradient", "wri_tile_count", "wri_tile_shape", "wri_strerror",
-           "wri_version")
+           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_tile_count", "wri_tile_shape",
+           "wri_strerror", "wri_version")
 
 
 def strerror(code: int) -> str:
@@ -242,6 +244,20 @@ def gradient(groups: Sequence[GroupSpec], dtype: int, alpha, grads=None, f=None,
     gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
     _check(lib.wri_gradient(m.arr, m.n, dtype, _ptr(a), gp, _ptr(f), _ptr(ws), ws.numel(), _stream(stream)),
            "wri_gradient")
+    return grads, f
+
+
+def gradient_noalloc(groups: Sequence[GroupSpec], dtype: int, alpha, grads, f, stream=None):
+    """wri_gradient_noalloc: like gradient() but without a workspace (static device scratch).
+
+    For callers that cannot allocate device memory; grads and f are caller-owned
+    tensors that are accumulated into."""
+    import torch
+    m = _Marshal(groups)
+    a = torch.view_as_real(alpha.to(torch.complex128).contiguous())
+    gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
+    _check(lib.wri_gradient_noalloc(m.arr, m.n, dtype, _ptr(a), gp, _ptr(f), _stream(stream)),
+           "wri_gradient_noalloc")
     return grads, f
 
 
