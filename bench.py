@@ -38,6 +38,8 @@ def parse():
     p.add_argument("--iters", type=int, default=300, help="CGLS iterations per system per step")
     p.add_argument("--nsrc", type=int, default=128)
     p.add_argument("--small", action="store_true", help="tiny workload (debugging only)")
+    p.add_argument("--only-group", type=int, default=-1,
+                   help="keep only one frequency group (0: 3 Hz, 1: 5 Hz, 2: 8 Hz); profiling cases")
     p.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU legs")
     return p.parse_args()
 
@@ -171,6 +173,8 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     groups = workload(args.nsrc, args.small)
+    if args.only_group >= 0:
+        groups = [groups[args.only_group]]
     specs = [to_device(g, wri.C64, dev) for g in groups]
     nsys = sum(g.nsys for g in groups)
     n_nodes = [g.spec.n for g in groups]

@@ -110,6 +110,8 @@ typedef struct {
                           (0 = library default) */
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
+  int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
+                          1 = z-march kernels only, 2 + c = TMA configuration c (0..3) */
 } wri_solve_opts;
 
 /* y = A x (wri_apply_A) or y = A^H x (wri_apply_AH) for `nsys` vectors that share the

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwri.so")
-SOURCES = ["wri_api.cu", "wri_k32.cu", "wri_k64.cu", "wri_small.cu"]
+SOURCES = ["wri_api.cu", "wri_k32.cu", "wri_k64.cu", "wri_small.cu", "wri_k32_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

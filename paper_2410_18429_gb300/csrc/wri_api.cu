@@ -9,8 +9,12 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/wri.h"
 #include "wri_launch.h"
+#include "wri_tma.cuh"
 
 using namespace wri;
 
@@ -64,6 +68,10 @@ AxisPml axis(int n, const wri_grid& g) {
     a.smax = 0.0;
     a.invL = 0.0;
   }
+  a.hf = (float)a.h;
+  a.inv_omegaf = (float)a.inv_omega;
+  a.smaxf = (float)a.smax;
+  a.invLf = (float)a.invL;
   return a;
 }
 
@@ -74,6 +82,8 @@ void fill_geom(GroupDev& G, const wri_grid& g) {
   G.npml = g.npml;
   G.h = g.h;
   G.omega = g.omega;
+  G.ih2f = (float)(1.0 / (g.h * g.h));
+  G.om2f = (float)(g.omega * g.omega);
   G.ax = axis(g.nx, g);
   G.ay = axis(g.ny, g);
   G.az = axis(g.nz, g);
@@ -125,6 +135,7 @@ int validate_groups(const wri_group* groups, int ngroups, bool need_data) {
 
 struct Plan {
   int ngroups = 0, nsys_total = 0, nnz_total = 0, dtype = 0, ir = 0, by = 8;
+  int tma_cfg = -1;  // TMA configuration of the CG phases, -1 = z-march kernels
   int vbytes = 8;   // bytes of one complex of the iteration vectors
   int rlbytes = 8;  // bytes of one complex of lamd / r2
   long long nitems = 0;
@@ -161,6 +172,16 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
   P.dtype = o->dtype;
   P.ir = (o->dtype == WRI_C64 && o->max_refine > 0) ? 1 : 0;
   P.by = by_of_tile(o->tile);
+  P.tma_cfg = -1;
+  if (!o->plain && o->kernel != 1 && o->dtype == WRI_C64 && !P.ir) {
+    bool ok = true;
+    for (int gi = 0; gi < ngroups; ++gi)
+      ok = ok && (groups[gi].grid.nx % 4 == 0) && ((uintptr_t)groups[gi].u % 16 == 0);
+    if (ok) {
+      P.tma_cfg = o->kernel >= 2 ? o->kernel - 2 : 0;
+      P.by = tma_config_by(P.tma_cfg);
+    }
+  }
   P.vbytes = (o->dtype == WRI_C128) ? 16 : 8;
   P.rlbytes = (o->dtype == WRI_C128 || P.ir) ? 16 : 8;
   long long xy_items = 0;
@@ -219,6 +240,7 @@ int validate_opts(const wri_solve_opts* o) {
   if (o->dtype != WRI_C64 && o->dtype != WRI_C128) return WRI_EINVAL;
   if (!(o->tol >= 0) || !std::isfinite(o->tol) || o->max_iter < 1) return WRI_EINVAL;
   if (o->max_refine < 0 || o->poll_every < 0 || o->tile < 0 || o->tile > 3 || o->zsplit < 0) return WRI_EINVAL;
+  if (o->kernel < 0 || o->kernel > 1 + tma_config_count()) return WRI_EINVAL;
   if (o->max_refine > 0) {
     if (o->dtype != WRI_C64) return WRI_ENOTSUP;
     if (!(o->refine_tol >= 0) || !(o->inner_tol > 0 && o->inner_tol < 1)) return WRI_EINVAL;
@@ -332,17 +354,73 @@ int poll_default(const Plan& P) {
   return std::max(2, std::min(k, 256));
 }
 
+// ---------------------------------------------------------------- TMA descriptors
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 4-D map over [nsys][nz][ny][nx] complex64 vectors (8-byte elements); box bx x by x 1 x 1
+bool encode_vec(CUtensorMap* m, const void* base, const GroupDev& G, int bx, int by) {
+  const cuuint64_t dims[4] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz, (cuuint64_t)G.nsys};
+  const cuuint64_t strides[3] = {(cuuint64_t)G.nx * 8, (cuuint64_t)G.nx * G.ny * 8, (cuuint64_t)G.n * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3-D map over the float model [nz][ny][nx]; box 32 x by x 1
+bool encode_model(CUtensorMap* m, const void* base, const GroupDev& G, int by) {
+  const cuuint64_t dims[3] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)G.nx * 4, (cuuint64_t)G.nx * G.ny * 4};
+  const cuuint32_t box[3] = {WRI_TX, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool build_tma(const Batch& b, const Plan& P, int* err, TmaSet& T) {
+  if (!encode_fn()) return false;
+  std::memset(&T, 0, sizeof(T));
+  T.err = err;
+  const int hw = WRI_TX + 4, hh = P.by + 2;
+  for (int gi = 0; gi < b.ngroups; ++gi) {
+    const GroupDev& G = b.g[gi];
+    bool ok = encode_vec(&T.map[gi][TM_S], G.s, G, hw, hh) && encode_vec(&T.map[gi][TM_P0], G.p[0], G, hw, hh) &&
+              encode_vec(&T.map[gi][TM_P1], G.p[1], G, hw, hh) && encode_vec(&T.map[gi][TM_X], G.x, G, WRI_TX, P.by) &&
+              encode_vec(&T.map[gi][TM_T1], G.t1, G, hw, hh) && encode_vec(&T.map[gi][TM_R0], G.r1[0], G, hw, hh) &&
+              encode_vec(&T.map[gi][TM_R1], G.r1[1], G, hw, hh) && encode_model(&T.map[gi][TM_M], G.m, G, P.by);
+    if (!ok) return false;
+  }
+  return true;
+}
+
 // Runs CG iterations (phase 1 + phase 2) in CUDA-graph batches of K until no system remains.
-int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, int max_iter, cudaStream_t st) {
+int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, int max_iter, cudaStream_t st,
+             const TmaSet* tma = nullptr) {
   DevCtx* c = ctx();
   if (!c) return WRI_ECUDA;
   const int rb = P.ir ? 4 : P.vbytes / 2;
+  const bool use_tma = tma && P.tma_cfg >= 0 && mode2 == M_P2;
   // graph lookup / capture
-  std::vector<unsigned char> key(sizeof(Batch) * 2 + 4 * sizeof(int));
+  std::vector<unsigned char> key(sizeof(Batch) * 2 + 5 * sizeof(int) + (use_tma ? sizeof(TmaSet) : 0));
   std::memcpy(key.data(), &b1, sizeof(Batch));
   std::memcpy(key.data() + sizeof(Batch), &b2, sizeof(Batch));
-  const int extra[4] = {mode2, K, P.by, rb};
+  const int extra[5] = {mode2, K, P.by, rb, use_tma ? P.tma_cfg : -1};
   std::memcpy(key.data() + 2 * sizeof(Batch), extra, sizeof(extra));
+  if (use_tma) std::memcpy(key.data() + 2 * sizeof(Batch) + sizeof(extra), tma, sizeof(TmaSet));
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -353,8 +431,13 @@ int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, 
       WRI_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
       cudaError_t err = cudaSuccess;
       for (int k = 0; k < K && err == cudaSuccess; ++k) {
-        err = march(rb, rb, M_P1, false, P.by, b1, c->cap);
-        if (err == cudaSuccess) err = march(rb, rb, mode2, true, P.by, b2, c->cap);
+        if (use_tma) {
+          err = launch_phase_tma(M_P1, P.tma_cfg, b1, *tma, 0, c->cap);
+          if (err == cudaSuccess) err = launch_phase_tma(M_P2, P.tma_cfg, b2, *tma, 0, c->cap);
+        } else {
+          err = march(rb, rb, M_P1, false, P.by, b1, c->cap);
+          if (err == cudaSuccess) err = march(rb, rb, mode2, true, P.by, b2, c->cap);
+        }
       }
       cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
       if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -378,8 +461,9 @@ int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, 
   for (;;) {
     WRI_CK(cudaGraphLaunch(exec, st));
     launched += K;
-    WRI_CK(cudaMemcpyAsync(c->pinned, b1.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WRI_CK(cudaMemcpyAsync(c->pinned, b1.remaining, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     WRI_CK(cudaStreamSynchronize(st));
+    if (c->pinned[1] != 0) return WRI_ECUDA;  // a bounded copy wait timed out
     if (*c->pinned <= 0) break;
     if (launched > (long long)max_iter + 2 * K + 2) return WRI_ECUDA;  // a system failed to stop
   }
@@ -408,7 +492,7 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   b.tol = o->tol;
   const int vb = P.vbytes / 2;
   WRI_CK(launch_setup_rhs(o->dtype == WRI_C128 ? 8 : 4, vb, b, P.nsys_total, st));
-  WRI_CK(cudaMemsetAsync(b.remaining, 0, sizeof(int), st));
+  WRI_CK(cudaMemsetAsync(b.remaining, 0, 2 * sizeof(int), st));
   if (o->warm_start) {
     Batch r = b;
     r.flavor = SH_REF;
@@ -425,6 +509,12 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   Batch b1 = b, b2 = b;
   b1.flavor = b2.flavor = 0;
   const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
+  if (P.tma_cfg >= 0) {
+    static thread_local TmaSet T;  // ~8 KB: kept off the stack
+    if (build_tma(b, P, b.remaining + 1, T))
+      return run_loop(P, b1, b2, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, &T);
+    // descriptors rejected (e.g. an unaligned model array): same decomposition, z-march kernels
+  }
   return run_loop(P, b1, b2, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st);
 }
 
@@ -461,7 +551,7 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
   }
   const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
   for (int outer_k = 0;; ++outer_k) {
-    WRI_CK(cudaMemsetAsync(outer.remaining, 0, sizeof(int), st));
+    WRI_CK(cudaMemsetAsync(outer.remaining, 0, 2 * sizeof(int), st));
     Batch r = outer;
     r.outer = outer_k;
     r.flavor = SH_REFINE;

@@ -56,21 +56,28 @@ __device__ __forceinline__ double2 to_c(double2 a, double) { return a; }
 // s(xi) = 1 + i sigma(xi)/omega, sigma = sigma_max (xi/L)^2, xi = distance into the
 // padding from the last physical node, measured at position `pos` (node units,
 // half-integers for the half points).  CONJ returns conj(s), used by A^H.
+// Parameters are kept in both precisions so FP32 kernels never convert from FP64
+// (conversions run on the FP64 pipe, which is narrow on GB300).
 struct AxisPml {
   int n, npml;
   double h, inv_omega, smax, invL;
+  float hf, inv_omegaf, smaxf, invLf;
 };
+
+template <typename R> __device__ __forceinline__ R pick(double d, float f);
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 template <typename R, bool CONJ>
 __device__ __forceinline__ cx<R> stretch_at(const AxisPml& a, R pos) {
   R xi = R(0);
   const R lo = R(a.npml), hi = R(a.n - 1 - a.npml);
   if (a.npml > 0) {
-    if (pos < lo) xi = (lo - pos) * R(a.h);
-    else if (pos > hi) xi = (pos - hi) * R(a.h);
+    if (pos < lo) xi = (lo - pos) * pick<R>(a.h, a.hf);
+    else if (pos > hi) xi = (pos - hi) * pick<R>(a.h, a.hf);
   }
-  const R q = xi * R(a.invL);
-  const R im = R(a.smax) * q * q * R(a.inv_omega);
+  const R q = xi * pick<R>(a.invL, a.invLf);
+  const R im = pick<R>(a.smax, a.smaxf) * q * q * pick<R>(a.inv_omega, a.inv_omegaf);
   return mkc(R(1), CONJ ? -im : im);
 }
 
@@ -122,6 +129,7 @@ struct SysDev {
 struct GroupDev {
   int nx, ny, nz, npml;
   double h, omega, lambda;
+  float ih2f, om2f, lambdaf;  // 1/h^2, omega^2, lambda in FP32
   AxisPml ax, ay, az;
   int nsys, sys0;          // systems of the group and global index of the first
   int tiles_x, tiles_y, zsplit, zc, ntiles;

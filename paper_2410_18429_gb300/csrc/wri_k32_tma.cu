@@ -1,0 +1,53 @@
+// TMA-pipelined CGLS phase kernels (complex64) and their launcher.
+#include "wri_launch.h"
+#include "wri_tma.cuh"
+
+namespace wri {
+
+template <int MODE, int BY, int S>
+static cudaError_t launch_one(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
+  static int occ = -1;
+  const size_t smem = TmaLayout<MODE, BY>::bytes(S);
+  auto kern = k_phase_tma<MODE, BY, S>;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, WRI_TX * BY, smem);
+    if (e != cudaSuccess) return e;
+    occ = n > 0 ? n : 1;
+  }
+  if (grid <= 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long g = (long long)sms * occ;
+    grid = (int)(g < b.nitems ? g : b.nitems);
+    if (grid < 1) grid = 1;
+  }
+  kern<<<grid, dim3(WRI_TX, BY), smem, st>>>(b, T);
+  return cudaGetLastError();
+}
+
+int tma_config_count() { return 4; }
+
+// config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4)
+int tma_config_by(int cfg) { return cfg >= 2 ? 16 : 8; }
+
+cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
+  if (b.nitems <= 0) return cudaSuccess;
+#define WRI_TMA_CASE(M, C_, BY_, S_) \
+  if (mode == M && cfg == C_) return launch_one<M, BY_, S_>(b, T, grid, st);
+  WRI_TMA_CASE(M_P1, 0, 8, 4)
+  WRI_TMA_CASE(M_P2, 0, 8, 4)
+  WRI_TMA_CASE(M_P1, 1, 8, 6)
+  WRI_TMA_CASE(M_P2, 1, 8, 6)
+  WRI_TMA_CASE(M_P1, 2, 16, 3)
+  WRI_TMA_CASE(M_P2, 2, 16, 3)
+  WRI_TMA_CASE(M_P1, 3, 16, 4)
+  WRI_TMA_CASE(M_P2, 3, 16, 4)
+#undef WRI_TMA_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace wri

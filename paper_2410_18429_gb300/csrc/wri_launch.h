@@ -35,3 +35,11 @@ cudaError_t plain_axpy(int rbytes, void* y, const void* x, double a, long long n
 cudaError_t plain_xpby(int rbytes, void* p, const void* s, double beta, long long n, cudaStream_t st);
 
 }  // namespace wri
+
+namespace wri {
+struct TmaSet;
+// TMA-pipelined phase 1 / phase 2 kernels (complex64); cfg selects tile height and stages.
+int tma_config_count();
+int tma_config_by(int cfg);
+cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st);
+}  // namespace wri

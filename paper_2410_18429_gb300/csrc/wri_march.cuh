@@ -55,10 +55,15 @@ struct XYCoef {
   cx<R> sx, sy, sxy, ixm, ixp, iym, iyp;  // ixm = 1/(s_x(i-1/2) h^2), ...
 };
 
+template <typename R>
+__device__ __forceinline__ R inv_h2(const GroupDev& G) {
+  return pick<R>(1.0 / (G.h * G.h), G.ih2f);
+}
+
 template <typename R, bool CONJ>
 __device__ __forceinline__ XYCoef<R> xy_coef(const GroupDev& G, int i, int j) {
   XYCoef<R> c;
-  const R ih2 = R(1) / (R(G.h) * R(G.h));
+  const R ih2 = inv_h2<R>(G);
   c.sx = stretch_at<R, CONJ>(G.ax, R(i));
   c.sy = stretch_at<R, CONJ>(G.ay, R(j));
   c.sxy = c.sx * c.sy;
@@ -77,7 +82,7 @@ struct ZCoef {
 template <typename R, bool CONJ>
 __device__ __forceinline__ ZCoef<R> z_coef(const GroupDev& G, int k) {
   ZCoef<R> c;
-  const R ih2 = R(1) / (R(G.h) * R(G.h));
+  const R ih2 = inv_h2<R>(G);
   c.sz = stretch_at<R, CONJ>(G.az, R(k));
   c.izm = ih2 * inv(stretch_at<R, CONJ>(G.az, R(k) - R(0.5)));
   c.izp = ih2 * inv(stretch_at<R, CONJ>(G.az, R(k) + R(0.5)));

@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
       interior_range(G.az, zlo, zhi);
       const bool xy_int = (x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi) && (y0 >= ylo) &&
                           (min(y0 + BY, ny) - 1 <= yhi);
-      const R om2 = R(G.omega) * R(G.omega);
-      const R ih2 = R(1) / (R(G.h) * R(G.h));
+      const R om2 = pick<R>(G.omega * G.omega, G.om2f);
+      const R ih2 = inv_h2<R>(G);
 
       if (MODE == M_GRAD) {
         for (int e = tid; e < GZ * BY * WRI_TX; e += NT) (&gacc[0][0][0])[e] = 0.0;
@@ -399,7 +399,8 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
               ((OC*)G.s)[gnode] = to_c(AF, OR(0));
             } else if (MODE == M_SH) {
               ((OC*)G.s)[gnode] = to_c(AF, OR(0));
-              accd += (double)abs2(AF);
+              if (sizeof(R) == 4) accf += (float)abs2(AF);
+              else accd += (double)abs2(AF);
             } else if (MODE == M_RES) {
               C r = czero<R>() - AF;
               if (node == src) r = G.masked ? czero<R>() : a_src - AF;

@@ -92,7 +92,7 @@ __device__ cx<R> apply_at(const GroupDev& G, const cx<R>* u, long long node) {
   };
   const XYCoef<R> c = xy_coef<R, false>(G, i, j);
   const ZCoef<R> z = z_coef<R, false>(G, k);
-  const R om2m = R(G.omega) * R(G.omega) * model_at<R>(G.m, G.m_double, node);
+  const R om2m = pick<R>(G.omega * G.omega, G.om2f) * model_at<R>(G.m, G.m_double, node);
   return stencil_general<R, false>(G, c, z, om2m, at(i, j, k), at(i - 1, j, k), at(i + 1, j, k),
                                    at(i, j - 1, k), at(i, j + 1, k), at(i, j, k - 1), at(i, j, k + 1));
 }

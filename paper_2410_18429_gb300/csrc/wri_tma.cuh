@@ -1,0 +1,313 @@
+// TMA-pipelined CGLS phases (complex64 stencil, FP64 reductions) for sm_103a.
+//
+// Same work decomposition and finalizers as the z-march of wri_march_impl.cuh, but the
+// planes of every input vector stream through a ring of S shared-memory stages filled
+// by cp.async.bulk.tensor (TMA) copies:
+//   * a halo'd field (the two vectors that form F) is copied as a 36 x (BY+2) box that
+//     starts at x0-2 (16-byte aligned) and y0-1; out-of-grid elements arrive as zeros,
+//     which is the Dirichlet boundary of the operator;
+//   * the iterate x and the model m are copied as 32 x BY boxes;
+//   * one thread arms an mbarrier per stage with the expected byte count and issues the
+//     copies S planes ahead, so every CTA keeps S planes of all its inputs in flight
+//     independently of its registers and warps.
+// The consumers form F = a + c b on the halo'd tile into a ring of 4 F planes (own
+// nodes stored as the updated CG vector), then apply the stencil one plane behind.
+// Every mbarrier wait is bounded: on time-out the CTA records an error flag, drains
+// its own copies (again bounded) and stops.
+#pragma once
+
+#include <cuda.h>
+
+#include "wri_march_impl.cuh"
+
+namespace wri {
+
+enum TmaMap : int { TM_S = 0, TM_P0, TM_P1, TM_X, TM_T1, TM_R0, TM_R1, TM_M, TM_COUNT };
+
+struct TmaSet {
+  CUtensorMap map[WRI_MAXG][TM_COUNT];
+  int* err;  // set to 1 by a CTA whose copy wait timed out
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false after ~2^24 polls (seconds), which only a broken copy can cause
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 24); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Shared-memory layout of one CTA.  Every TMA destination starts on a 128-byte boundary
+// (the bulk tensor copy requires it): each box is padded to a multiple of 128 bytes and
+// the dynamic region is re-aligned at run time (bytes() includes 128 bytes of slack).
+template <int MODE, int BY>
+struct TmaLayout {
+  static constexpr int HW = WRI_TX + 4;  // halo box width: x0-2 .. x0+33
+  static constexpr int HH = BY + 2;      // halo box height: y0-1 .. y0+BY
+  static constexpr int FW = WRI_TX + 2;  // F tile width: x0-1 .. x0+32
+  static constexpr int pad(int v) { return (v + 127) / 128 * 128; }
+  static constexpr int HALO = HW * HH * 8;     // bytes copied per halo box
+  static constexpr int CTR = WRI_TX * BY * 8;  // bytes copied per 32 x BY complex box
+  static constexpr int MB = WRI_TX * BY * 4;   // bytes copied per 32 x BY float box
+  static constexpr int OFF_B = pad(HALO);
+  static constexpr int OFF_X = OFF_B + pad(HALO);
+  static constexpr int OFF_M = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);
+  static constexpr int STAGE = OFF_M + pad(MB);
+  static constexpr int FRING = 4 * HH * FW * 8;
+  static size_t bytes(int S) { return 128 + (size_t)S * STAGE + FRING + 8 * S; }
+};
+
+template <int MODE, int BY, int S>
+__global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant__ Batch b,
+                                                          const __grid_constant__ TmaSet T) {
+  static_assert(MODE == M_P1 || MODE == M_P2, "TMA path covers the two CGLS phases");
+  typedef float2 C;
+  typedef TmaLayout<MODE, BY> L;
+  constexpr bool CONJ = (MODE == M_P2);
+  constexpr int NT = WRI_TX * BY;
+  constexpr int RING = 2 * WRI_TX + 2 * BY;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red[NT / 32];
+  __shared__ double bcast;
+  __shared__ int s_last;
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  C(*F)[L::HH][L::FW] = reinterpret_cast<C(*)[L::HH][L::FW]>(smem + (size_t)S * L::STAGE);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::STAGE + L::FRING);
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * WRI_TX + tx;
+  // self-check of the copy destinations (uniform): never issue a misaligned bulk copy
+  if ((smem_addr(smem) & 127u) != 0u || (L::OFF_B & 127) || (L::OFF_X & 127) || (L::OFF_M & 127) ||
+      (L::STAGE & 127)) {
+    if (tid == 0) atomicExch(T.err, 2);
+    return;
+  }
+  if (tid == 0)
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+  __syncthreads();
+  unsigned uses = 0;  // stage uses so far (uniform across the CTA)
+
+  for (long long item = blockIdx.x; item < b.nitems; item += gridDim.x) {
+    const int gi = find_group(b, item);
+    const GroupDev& G = b.g[gi];
+    const long long local = item - G.item0;
+    const int sl = (int)(local % G.nsys);
+    const int tile = (int)(local / G.nsys);
+    SysDev* sd = b.sys + (G.sys0 + sl);
+    const int state = sd->state;
+    if (MODE == M_P1 ? (state == ST_DONE) : (state != ST_ACTIVE)) continue;
+    const bool xonly = (MODE == M_P1 && state == ST_FINISHING);
+
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int tzi = tile % G.zsplit;
+    const int txy = tile / G.zsplit;
+    const int x0 = (txy % G.tiles_x) * WRI_TX;
+    const int y0 = (txy / G.tiles_x) * BY;
+    const int z0 = tzi * G.zc;
+    const int z1 = min(z0 + G.zc, nz);
+    const int i = x0 + tx, j = y0 + ty;
+    const bool own = (i < nx) && (j < ny);
+    const long long plane = (long long)nx * ny;
+    const long long col = (long long)j * nx + i;
+    const long long off = (long long)sl * G.n;
+    const int iter = sd->iter;
+    const int cur = iter & 1;
+    double accd = 0.0;
+
+    if (xonly) {
+      C* X = (C*)G.x + off;
+      const C* Pc = (const C*)G.p[cur] + off;
+      const float a = (float)sd->alpha;
+      if (own)
+        for (int k = z0; k < z1; ++k) {
+          const long long node = k * plane + col;
+          X[node] = X[node] + a * __ldg(Pc + node);
+        }
+    } else {
+      const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
+      const bool hasB = (MODE == M_P2) || iter > 0;
+      const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
+      const bool hasX = (MODE == M_P1) && iter > 0;
+      const CUtensorMap* mapX = &T.map[gi][TM_X];
+      const CUtensorMap* mapM = &T.map[gi][TM_M];
+      const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + L::MB;
+      const float coef = (MODE == M_P1) ? (float)sd->beta : -(float)sd->alpha;
+      const float xal = (float)sd->alpha;
+      C* Fst = (MODE == M_P1) ? (C*)G.p[cur ^ 1] + off : (C*)G.r1[cur ^ 1] + off;
+      C* X = (C*)G.x + off;
+      C* OUT = (MODE == M_P1) ? (C*)G.t1 + off : (C*)G.s + off;
+      const long long src = sd->src;
+      const int count = z1 - z0 + 2;  // planes z0-1 .. z1
+
+      auto issue = [&](int q) {
+        const int st = (int)((uses + q) % S);
+        unsigned char* base = smem + (size_t)st * L::STAGE;
+        const int kq = z0 - 1 + q;
+        mbar_expect_tx(&bar[st], tx_bytes);
+        tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &bar[st]);
+        if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &bar[st]);
+        if (hasX) tma_load_4d(base + L::OFF_X, mapX, x0, y0, kq, sl, &bar[st]);
+        tma_load_3d(base + L::OFF_M, mapM, x0, y0, kq, &bar[st]);
+      };
+
+      const XYCoef<float> cxy = xy_coef<float, CONJ>(G, min(i, nx - 1), min(j, ny - 1));
+      int xlo, xhi, ylo, yhi, zlo, zhi;
+      interior_range(G.ax, xlo, xhi);
+      interior_range(G.ay, ylo, yhi);
+      interior_range(G.az, zlo, zhi);
+      const bool xy_int =
+          (x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi) && (y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi);
+      const float om2 = G.om2f;
+      const float ih2 = G.ih2f;
+
+      __syncthreads();  // the previous item no longer reads the stages or the F ring
+      if (tid == 0)
+        for (int q = 0; q < S && q < count; ++q) issue(q);
+
+      float accf = 0.f;
+      float m_prev = 0.f;
+      int issued = min(S, count);
+      int q_fail = -1;
+      for (int q = 0; q < count; ++q) {
+        const int st = (int)((uses + q) % S);
+        const uint32_t par = ((uses + q) / S) & 1u;
+        const bool ok = mbar_wait(&bar[st], par);
+        if (__syncthreads_or(!ok)) {
+          q_fail = q;
+          break;
+        }
+        const unsigned char* base = smem + (size_t)st * L::STAGE;
+        const C(*A)[L::HW] = reinterpret_cast<const C(*)[L::HW]>(base);
+        const C(*B)[L::HW] = reinterpret_cast<const C(*)[L::HW]>(base + L::OFF_B);
+        const C(*XT)[WRI_TX] = reinterpret_cast<const C(*)[WRI_TX]>(base + L::OFF_X);
+        const float(*MT)[WRI_TX] = reinterpret_cast<const float(*)[WRI_TX]>(base + L::OFF_M);
+        const int kq = z0 - 1 + q;
+        const int fb = q & 3;
+        // F on the own node (stored as the updated CG vector on own planes)
+        {
+          const C a = A[ty + 1][tx + 2];
+          C v = a;
+          if (hasB) {
+            const C bb = B[ty + 1][tx + 2];
+            v = a + coef * bb;
+            if (MODE == M_P1 && own && kq >= z0 && kq < z1) {
+              const long long node = kq * plane + col;
+              X[node] = XT[ty][tx] + xal * bb;
+            }
+          }
+          F[fb][ty + 1][tx + 1] = v;
+          if (own && kq >= z0 && kq < z1) Fst[kq * plane + col] = v;
+        }
+        const float m_new = MT[ty][tx];
+        // F on the halo ring (zeros outside the grid come from the copies)
+        for (int e = tid; e < RING; e += NT) {
+          int si, sj;
+          if (e < WRI_TX) { si = e + 1; sj = 0; }
+          else if (e < 2 * WRI_TX) { si = e - WRI_TX + 1; sj = BY + 1; }
+          else if (e < 2 * WRI_TX + BY) { si = 0; sj = e - 2 * WRI_TX + 1; }
+          else { si = WRI_TX + 1; sj = e - 2 * WRI_TX - BY + 1; }
+          const C a = A[sj][si + 1];
+          F[fb][sj][si] = hasB ? a + coef * B[sj][si + 1] : a;
+        }
+        __syncthreads();
+        if (tid == 0 && issued < count) {
+          issue(issued);
+          ++issued;
+        }
+        if (q >= 2) {
+          const int kp = kq - 1;  // plane of the stencil
+          const int fm = (q - 2) & 3, fc = (q - 1) & 3;
+          const C u = F[fc][ty + 1][tx + 1];
+          const C uxm = F[fc][ty + 1][tx];
+          const C uxp = F[fc][ty + 1][tx + 2];
+          const C uym = F[fc][ty][tx + 1];
+          const C uyp = F[fc][ty + 2][tx + 1];
+          const C uzm = F[fm][ty + 1][tx + 1];
+          const C uzp = F[fb][ty + 1][tx + 1];
+          const float om2m = om2 * m_prev;
+          C AF;
+          if (xy_int && kp >= zlo && kp <= zhi) {
+            AF = stencil_interior<float>(ih2, om2m, u, uxm, uxp, uym, uyp, uzm, uzp);
+          } else {
+            const ZCoef<float> zc = z_coef<float, CONJ>(G, kp);
+            AF = stencil_general<float, CONJ>(G, cxy, zc, om2m, u, uxm, uxp, uym, uyp, uzm, uzp);
+          }
+          if (own) {
+            const long long node = kp * plane + col;
+            C o = AF;
+            if (MODE == M_P1 && G.masked && node == src) o = czero<float>();
+            OUT[node] = o;
+            accf += abs2(o);
+          }
+          if (((q - 2) & 7) == 7) {
+            accd += (double)accf;
+            accf = 0.f;
+          }
+        }
+        m_prev = m_new;
+      }
+      if (q_fail >= 0) {
+        // a copy never completed: record it, drain the copies this CTA issued (bounded), stop
+        if (tid == 0) {
+          atomicExch(T.err, 1);
+          for (int qq = q_fail; qq < issued; ++qq) mbar_wait(&bar[(uses + qq) % S], ((uses + qq) / S) & 1u);
+        }
+        __syncthreads();
+        return;
+      }
+      uses += (unsigned)count;
+      accd += (double)accf;
+    }
+
+    // ---- tile partial, ticket, and the system's finalizer (shared with the generic kernel)
+    const double tsum = block_sum<NT>(accd, red);
+    if (tid == 0 && !xonly) b.partial[sd->part_off + tile] = tsum;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned t = atomicAdd(&sd->ticket, 1u);
+      s_last = (t == (unsigned)(G.ntiles - 1));
+    }
+    __syncthreads();
+    if (s_last) finalize<float, float, MODE, BY>(b, G, sd, sl, xonly, red, &bcast);
+  }
+}
+
+}  // namespace wri

@@ -38,7 +38,7 @@ class WriSolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("dtype", C.c_int32),
                 ("warm_start", C.c_int32), ("max_refine", C.c_int32), ("refine_tol", C.c_double),
                 ("inner_tol", C.c_double), ("plain", C.c_int32), ("poll_every", C.c_int32),
-                ("tile", C.c_int32), ("zsplit", C.c_int32)]
+                ("tile", C.c_int32), ("zsplit", C.c_int32), ("kernel", C.c_int32)]
 
 
 class WriError(RuntimeError):
@@ -161,11 +161,18 @@ class _Marshal:
         self.n = len(groups)
 
 
+KERNEL_AUTO, KERNEL_MARCH = 0, 1
+
+
+def KERNEL_TMA(cfg: int = 0) -> int:
+    return 2 + int(cfg)
+
+
 def make_opts(tol=1e-6, max_iter=10000, dtype=C64, warm_start=False, max_refine=0, refine_tol=1e-10,
-              inner_tol=1e-3, plain=False, poll_every=0, tile=0, zsplit=0) -> WriSolveOpts:
+              inner_tol=1e-3, plain=False, poll_every=0, tile=0, zsplit=0, kernel=KERNEL_AUTO) -> WriSolveOpts:
     return WriSolveOpts(float(tol), int(max_iter), int(dtype), int(bool(warm_start)), int(max_refine),
                         float(refine_tol), float(inner_tol), int(bool(plain)), int(poll_every), int(tile),
-                        int(zsplit))
+                        int(zsplit), int(kernel))
 
 
 def workspace_size(groups: Sequence[GroupSpec], opts: WriSolveOpts) -> int:

@@ -88,6 +88,46 @@ def test_fixed_iterations_match_oracle_cgls(W, dtype, tol, source_free):
         assert abs(rr.cpu().numpy()[s] - rr_k) <= max(tol, 1e-6) * rr_k * 10
 
 
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("source_free", [True, False])
+def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
+    """TMA-pipelined phases (x extent a multiple of 4): ragged 32 x BY tiles, iterates of
+    k CGLS steps equal the oracle's and the z-march kernels' (same tile height)."""
+    G = case(nphys=(36, 13, 10), npml=4, nsys=3)
+    m, d, al = seen(G, True)
+    A = oracle_A(G, m)
+    k = 25
+    by = 16 if cfg >= 2 else 8
+    s_t, s_m = _spec(W, G, 0, source_free), _spec(W, G, 0, source_free)
+    it_t, rr_t, st_t = W.solve([s_t], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_TMA(cfg)))
+    it_m, rr_m, st_m = W.solve([s_m], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_MARCH,
+                                                 tile=3 if by == 16 else 2))
+    assert it_t.cpu().tolist() == [k] * 3
+    u_t, u_m = s_t.u.cpu().numpy(), s_m.u.cpu().numpy()
+    assert rel(u_t, u_m) < 1e-5
+    for s in range(3):
+        rec = G.rec_idx[G.rec_off[s]:G.rec_off[s + 1]]
+        S = O.augmented_operator(A, O.restriction(G.spec.n, rec), G.src[s], G.lam, source_free)
+        b = O.rhs(G.spec.n, G.src[s], d[G.rec_off[s]:G.rec_off[s + 1]], G.lam, al[s], source_free)
+        x_k, _, _ = O.cgls(S, b, tol=0.0, max_iter=k)
+        assert rel(u_t[s], x_k) < 3e-4
+
+
+def test_tma_z_chunks_and_convergence(W):
+    """TMA path with z-chunks and a real stopping test: same iterations (within 5 %) and
+    wavefields as the z-march kernels at tolerance 1e-3."""
+    G = case(nphys=(28, 16, 14), npml=4, nsys=2)
+    s_t, s_m = _spec(W, G, 0), _spec(W, G, 0)
+    it_t, rr_t, st_t = W.solve([s_t], W.make_opts(tol=1e-3, max_iter=100000, dtype=0, zsplit=3,
+                                                 kernel=W.KERNEL_TMA(0)))
+    it_m, rr_m, st_m = W.solve([s_m], W.make_opts(tol=1e-3, max_iter=100000, dtype=0, zsplit=3,
+                                                 kernel=W.KERNEL_MARCH))
+    assert st_t.cpu().tolist() == [0, 0]
+    a, b = it_t.cpu().numpy(), it_m.cpu().numpy()
+    assert np.all(np.abs(a - b) <= 0.05 * b + 2)
+    assert rel(s_t.u.cpu().numpy(), s_m.u.cpu().numpy()) < 2e-2
+
+
 # ------------------------------------------------------------------ converged solves (a3, a6)
 def _exact(G, m, d, source_free, s):
     A = oracle_A(G, m)
