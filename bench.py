@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--only-group", type=int, default=-1,
                    help="keep only one frequency group (0: 3 Hz, 1: 5 Hz, 2: 8 Hz); profiling cases")
     p.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU legs")
+    p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 z-march only, 2+c TMA configuration c")
     return p.parse_args()
 
 
@@ -179,7 +180,7 @@ def main():
     nsys = sum(g.nsys for g in groups)
     n_nodes = [g.spec.n for g in groups]
     K = 2
-    opts = wri.make_opts(tol=0.0, max_iter=args.iters, dtype=wri.C64, poll_every=K)
+    opts = wri.make_opts(tol=0.0, max_iter=args.iters, dtype=wri.C64, poll_every=K, kernel=args.kernel)
     wsz = wri.workspace_size(specs, opts)
     work = torch.empty(wsz, dtype=torch.uint8, device=dev)
     grads = [torch.zeros(g.spec.nz, g.spec.ny, g.spec.nx, dtype=torch.float64, device=dev) for g in groups]
@@ -230,7 +231,7 @@ def main():
 
     # ---- roofline of the fused CG iteration (phase 1 + phase 2 kernels), live with CUDA events
     def timed_solve(iters):
-        o = wri.make_opts(tol=0.0, max_iter=iters, dtype=wri.C64, poll_every=K)
+        o = wri.make_opts(tol=0.0, max_iter=iters, dtype=wri.C64, poll_every=K, kernel=args.kernel)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)

@@ -8,9 +8,11 @@ template <int MODE, int BY, int S>
 static cudaError_t launch_one(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   static int occ = -1;
   const size_t smem = TmaLayout<MODE, BY>::bytes(S);
-  auto kern = k_phase_tma<MODE, BY, S>;
+  auto kern = k_phase_tma<MODE, BY, S, (BY <= 8 ? 3 : 1)>;
   if (occ < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, WRI_TX * BY, smem);

@@ -94,22 +94,37 @@ struct TmaLayout {
   static size_t bytes(int S) { return 128 + (size_t)S * STAGE + FRING + 8 * S; }
 };
 
-template <int MODE, int BY, int S>
-__global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant__ Batch b,
-                                                          const __grid_constant__ TmaSet T) {
+// Neumaier-compensated FP32 accumulation of non-negative terms: the per-thread part of
+// the FP64 reductions, kept in FP32 because GB300's FP64 pipe is narrow.
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v;
+    c += (s >= v) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <int MODE, int BY, int S, int MINB>
+__global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_constant__ Batch b,
+                                                                const __grid_constant__ TmaSet T) {
   static_assert(MODE == M_P1 || MODE == M_P2, "TMA path covers the two CGLS phases");
   typedef float2 C;
   typedef TmaLayout<MODE, BY> L;
   constexpr bool CONJ = (MODE == M_P2);
   constexpr int NT = WRI_TX * BY;
   constexpr int RING = 2 * WRI_TX + 2 * BY;
+  static_assert(RING <= NT, "one halo-ring element per thread");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red[NT / 32];
   __shared__ double bcast;
   __shared__ int s_last;
+  __shared__ C zring[4][3];  // stretch coefficients (s_z, 1/(s_z(k-1/2) h^2), 1/(s_z(k+1/2) h^2)) per plane
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-  C(*F)[L::HH][L::FW] = reinterpret_cast<C(*)[L::HH][L::FW]>(smem + (size_t)S * L::STAGE);
+  C* Fbase = reinterpret_cast<C*>(smem + (size_t)S * L::STAGE);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::STAGE + L::FRING);
+  constexpr int FPL = L::HH * L::FW;  // elements of one F plane
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * WRI_TX + tx;
@@ -119,6 +134,19 @@ __global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant_
     if (tid == 0) atomicExch(T.err, 2);
     return;
   }
+  // this thread's halo-ring element (fixed for the whole kernel)
+  const bool has_ring = tid < RING;
+  int r_si = 0, r_sj = 0;
+  if (tid < WRI_TX) { r_si = tid + 1; r_sj = 0; }
+  else if (tid < 2 * WRI_TX) { r_si = tid - WRI_TX + 1; r_sj = BY + 1; }
+  else if (tid < 2 * WRI_TX + BY) { r_si = 0; r_sj = tid - 2 * WRI_TX + 1; }
+  else { r_si = WRI_TX + 1; r_sj = tid - 2 * WRI_TX - BY + 1; }
+  const int r_raw = r_sj * L::HW + r_si + 1;   // element in a halo box
+  const int r_f = r_sj * L::FW + r_si;         // element in an F plane
+  const int o_raw = (ty + 1) * L::HW + tx + 2;  // own node in a halo box
+  const int o_f = (ty + 1) * L::FW + tx + 1;    // own node in an F plane
+  const int o_ctr = ty * WRI_TX + tx;           // own node in a 32 x BY box
+
   if (tid == 0)
     for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
   __syncthreads();
@@ -152,13 +180,13 @@ __global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant_
     double accd = 0.0;
 
     if (xonly) {
-      C* X = (C*)G.x + off;
-      const C* Pc = (const C*)G.p[cur] + off;
+      C* X = (C*)G.x + off + col;
+      const C* Pc = (const C*)G.p[cur] + off + col;
       const float a = (float)sd->alpha;
       if (own)
         for (int k = z0; k < z1; ++k) {
-          const long long node = k * plane + col;
-          X[node] = X[node] + a * __ldg(Pc + node);
+          const long long o = k * plane;
+          X[o] = X[o] + a * __ldg(Pc + o);
         }
     } else {
       const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
@@ -170,10 +198,18 @@ __global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant_
       const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + L::MB;
       const float coef = (MODE == M_P1) ? (float)sd->beta : -(float)sd->alpha;
       const float xal = (float)sd->alpha;
-      C* Fst = (MODE == M_P1) ? (C*)G.p[cur ^ 1] + off : (C*)G.r1[cur ^ 1] + off;
-      C* X = (C*)G.x + off;
-      C* OUT = (MODE == M_P1) ? (C*)G.t1 + off : (C*)G.s + off;
-      const long long src = sd->src;
+      // own-node pointers (plane offsets are added in the loop)
+      C* pF = ((MODE == M_P1) ? (C*)G.p[cur ^ 1] : (C*)G.r1[cur ^ 1]) + off + col;
+      C* pX = (C*)G.x + off + col;
+      C* pO = ((MODE == M_P1) ? (C*)G.t1 : (C*)G.s) + off + col;
+      // the masked source node as (plane, column) of this system, or none
+      int src_k = -1;
+      long long src_col = -1;
+      if (MODE == M_P1 && G.masked) {
+        src_k = (int)(sd->src / plane);
+        src_col = sd->src - (long long)src_k * plane;
+      }
+      const bool own_src_col = (src_col == col);
       const int count = z1 - z0 + 2;  // planes z0-1 .. z1
 
       auto issue = [&](int q) {
@@ -196,16 +232,18 @@ __global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant_
           (x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi) && (y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi);
       const float om2 = G.om2f;
       const float ih2 = G.ih2f;
+      const AxisPml az = G.az;
 
-      __syncthreads();  // the previous item no longer reads the stages or the F ring
+      __syncthreads();  // the previous item no longer reads the stages, the F ring or zring
       if (tid == 0)
         for (int q = 0; q < S && q < count; ++q) issue(q);
 
-      float accf = 0.f;
+      CompSum acc;
       float m_prev = 0.f;
       int issued = min(S, count);
       int q_fail = -1;
-      for (int q = 0; q < count; ++q) {
+      long long po = (long long)(z0 - 1) * plane;  // offset of plane kq
+      for (int q = 0; q < count; ++q, po += plane) {
         const int st = (int)((uses + q) % S);
         const uint32_t par = ((uses + q) / S) & 1u;
         const bool ok = mbar_wait(&bar[st], par);
@@ -214,37 +252,34 @@ __global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant_
           break;
         }
         const unsigned char* base = smem + (size_t)st * L::STAGE;
-        const C(*A)[L::HW] = reinterpret_cast<const C(*)[L::HW]>(base);
-        const C(*B)[L::HW] = reinterpret_cast<const C(*)[L::HW]>(base + L::OFF_B);
-        const C(*XT)[WRI_TX] = reinterpret_cast<const C(*)[WRI_TX]>(base + L::OFF_X);
-        const float(*MT)[WRI_TX] = reinterpret_cast<const float(*)[WRI_TX]>(base + L::OFF_M);
+        const C* A = reinterpret_cast<const C*>(base);
+        const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
+        const C* XT = reinterpret_cast<const C*>(base + L::OFF_X);
+        const float* MT = reinterpret_cast<const float*>(base + L::OFF_M);
         const int kq = z0 - 1 + q;
-        const int fb = q & 3;
+        C* Fq = Fbase + (q & 3) * FPL;
+        const bool mine = own && kq >= z0 && kq < z1;
         // F on the own node (stored as the updated CG vector on own planes)
         {
-          const C a = A[ty + 1][tx + 2];
+          const C a = A[o_raw];
           C v = a;
           if (hasB) {
-            const C bb = B[ty + 1][tx + 2];
+            const C bb = B[o_raw];
             v = a + coef * bb;
-            if (MODE == M_P1 && own && kq >= z0 && kq < z1) {
-              const long long node = kq * plane + col;
-              X[node] = XT[ty][tx] + xal * bb;
-            }
+            if (MODE == M_P1 && mine) pX[po] = XT[o_ctr] + xal * bb;
           }
-          F[fb][ty + 1][tx + 1] = v;
-          if (own && kq >= z0 && kq < z1) Fst[kq * plane + col] = v;
+          Fq[o_f] = v;
+          if (mine) pF[po] = v;
         }
-        const float m_new = MT[ty][tx];
-        // F on the halo ring (zeros outside the grid come from the copies)
-        for (int e = tid; e < RING; e += NT) {
-          int si, sj;
-          if (e < WRI_TX) { si = e + 1; sj = 0; }
-          else if (e < 2 * WRI_TX) { si = e - WRI_TX + 1; sj = BY + 1; }
-          else if (e < 2 * WRI_TX + BY) { si = 0; sj = e - 2 * WRI_TX + 1; }
-          else { si = WRI_TX + 1; sj = e - 2 * WRI_TX - BY + 1; }
-          const C a = A[sj][si + 1];
-          F[fb][sj][si] = hasB ? a + coef * B[sj][si + 1] : a;
+        const float m_new = MT[o_ctr];
+        // F on this thread's halo-ring element (zeros outside the grid come from the copies)
+        if (has_ring) Fq[r_f] = hasB ? A[r_raw] + coef * B[r_raw] : A[r_raw];
+        // z coefficients of plane kq, used by the stencil of the next iteration
+        if (tid == 32) {
+          const float ih2z = ih2;
+          zring[q & 3][0] = stretch_at<float, CONJ>(az, float(kq));
+          zring[q & 3][1] = ih2z * inv(stretch_at<float, CONJ>(az, float(kq) - 0.5f));
+          zring[q & 3][2] = ih2z * inv(stretch_at<float, CONJ>(az, float(kq) + 0.5f));
         }
         __syncthreads();
         if (tid == 0 && issued < count) {
@@ -253,32 +288,32 @@ __global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant_
         }
         if (q >= 2) {
           const int kp = kq - 1;  // plane of the stencil
-          const int fm = (q - 2) & 3, fc = (q - 1) & 3;
-          const C u = F[fc][ty + 1][tx + 1];
-          const C uxm = F[fc][ty + 1][tx];
-          const C uxp = F[fc][ty + 1][tx + 2];
-          const C uym = F[fc][ty][tx + 1];
-          const C uyp = F[fc][ty + 2][tx + 1];
-          const C uzm = F[fm][ty + 1][tx + 1];
-          const C uzp = F[fb][ty + 1][tx + 1];
+          const C* Fm = Fbase + ((q - 2) & 3) * FPL;
+          const C* Fc = Fbase + ((q - 1) & 3) * FPL;
+          const C u = Fc[o_f];
+          const C uxm = Fc[o_f - 1];
+          const C uxp = Fc[o_f + 1];
+          const C uym = Fc[o_f - L::FW];
+          const C uyp = Fc[o_f + L::FW];
+          const C uzm = Fm[o_f];
+          const C uzp = Fq[o_f];
           const float om2m = om2 * m_prev;
           C AF;
           if (xy_int && kp >= zlo && kp <= zhi) {
             AF = stencil_interior<float>(ih2, om2m, u, uxm, uxp, uym, uyp, uzm, uzp);
           } else {
-            const ZCoef<float> zc = z_coef<float, CONJ>(G, kp);
+            ZCoef<float> zc;
+            const C* zr = zring[(q - 1) & 3];
+            zc.sz = zr[0];
+            zc.izm = zr[1];
+            zc.izp = zr[2];
             AF = stencil_general<float, CONJ>(G, cxy, zc, om2m, u, uxm, uxp, uym, uyp, uzm, uzp);
           }
           if (own) {
-            const long long node = kp * plane + col;
             C o = AF;
-            if (MODE == M_P1 && G.masked && node == src) o = czero<float>();
-            OUT[node] = o;
-            accf += abs2(o);
-          }
-          if (((q - 2) & 7) == 7) {
-            accd += (double)accf;
-            accf = 0.f;
+            if (MODE == M_P1 && own_src_col && kp == src_k) o = czero<float>();
+            pO[po - plane] = o;
+            acc.add(abs2(o));
           }
         }
         m_prev = m_new;
@@ -293,7 +328,7 @@ __global__ void __launch_bounds__(WRI_TX* BY) k_phase_tma(const __grid_constant_
         return;
       }
       uses += (unsigned)count;
-      accd += (double)accf;
+      accd = acc.value();
     }
 
     // ---- tile partial, ticket, and the system's finalizer (shared with the generic kernel)
