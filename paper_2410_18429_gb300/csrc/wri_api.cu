@@ -145,6 +145,7 @@ struct Plan {
   GroupDev g[WRI_MAXG];
   size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][2], v_s[WRI_MAXG], v_t1[WRI_MAXG];
   size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG];
+  size_t off_ztab[WRI_MAXG];
   std::vector<int> rec_base;  // first receiver entry of every group
 };
 
@@ -216,6 +217,10 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
   off += align_up((size_t)P.rlbytes * std::max(P.nnz_total, 1));
   P.off_r2 = off;
   off += align_up((size_t)P.rlbytes * std::max(P.nnz_total, 1));
+  for (int gi = 0; gi < ngroups; ++gi) {
+    P.off_ztab[gi] = off;
+    off += align_up(sizeof(float) * 2 * 2 * 3 * (size_t)groups[gi].grid.nz);
+  }
   for (int gi = 0; gi < ngroups; ++gi) {
     const size_t vb = align_up((size_t)P.vbytes * (size_t)P.g[gi].nsys * (size_t)P.g[gi].n);
     P.v_r1[gi][0] = off; off += vb;
@@ -341,6 +346,7 @@ Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_
     G.x = (P.ir && inner_view) ? (void*)(ws + P.v_x32[gi]) : U.u;
     G.x64 = P.ir ? ws + P.v_x64[gi] : nullptr;
     G.r64 = P.ir ? ws + P.v_r64[gi] : nullptr;
+    G.ztab = (const float2*)(ws + P.off_ztab[gi]);
     b.g[gi] = G;
   }
   return b;
@@ -510,6 +516,7 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   b1.flavor = b2.flavor = 0;
   const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
   if (P.tma_cfg >= 0) {
+    WRI_CK(launch_ztable(b, st));
     static thread_local TmaSet T;  // ~8 KB: kept off the stack
     if (build_tma(b, P, b.remaining + 1, T))
       return run_loop(P, b1, b2, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, &T);

@@ -148,6 +148,8 @@ struct GroupDev {
   void* x64;                // [nsys][n] double2 refinement master (or null)
   void* r64;                // [nsys][n] double2 FP64 residual (or null)
   double* grad;             // [n] gradient accumulator (gradient kernel only)
+  const float2* ztab;       // [2][nz][3] z-axis coefficients (s_z, 1/(s_z(k-1/2) h^2), 1/(s_z(k+1/2) h^2)),
+                            // [0] for A, [1] conjugated for A^H; FP32, built once per solve
 };
 
 struct Batch {

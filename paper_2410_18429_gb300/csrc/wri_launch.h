@@ -16,6 +16,7 @@ cudaError_t launch_march_f64_to_f32(int mode, int by, const Batch& b, int grid, 
 
 // small kernels (wri_small.cu)
 cudaError_t launch_setup_rhs(int dtype_bytes, int rl_bytes, const Batch& b, int nsys_total, cudaStream_t st);
+cudaError_t launch_ztable(const Batch& b, cudaStream_t st);
 cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* relres, int32_t* status,
                           cudaStream_t st);
 cudaError_t launch_ir_init(const Batch& b, int warm, cudaStream_t st);

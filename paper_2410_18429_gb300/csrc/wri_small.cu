@@ -21,6 +21,11 @@ cudaError_t launch_setup_rhs(int dtype_bytes, int rl_bytes, const Batch& b, int 
   return cudaGetLastError();
 }
 
+cudaError_t launch_ztable(const Batch& b, cudaStream_t st) {
+  k_ztable<<<dim3(4, b.ngroups), 128, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* relres, int32_t* status,
                           cudaStream_t st) {
   k_export<<<(nsys + 127) / 128, 128, 0, st>>>(sys, nsys, iters, relres, status);

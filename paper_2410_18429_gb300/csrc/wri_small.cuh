@@ -27,6 +27,25 @@ __global__ void k_setup_rhs(const __grid_constant__ Batch b, int nsys_total) {
   }
 }
 
+// z-axis coefficient tables of every group (FP32): one thread per (group, plane).
+__global__ void k_ztable(const __grid_constant__ Batch b) {
+  const int g = blockIdx.y;
+  if (g >= b.ngroups) return;
+  const GroupDev& G = b.g[g];
+  float2* t = const_cast<float2*>(G.ztab);
+  if (!t) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.nz; k += gridDim.x * blockDim.x) {
+    const ZCoef<float> a = z_coef<float, false>(G, k);
+    const ZCoef<float> h = z_coef<float, true>(G, k);
+    t[3 * k + 0] = a.sz;
+    t[3 * k + 1] = a.izm;
+    t[3 * k + 2] = a.izp;
+    t[3 * (G.nz + k) + 0] = h.sz;
+    t[3 * (G.nz + k) + 1] = h.izm;
+    t[3 * (G.nz + k) + 2] = h.izp;
+  }
+}
+
 __global__ void k_export(const SysDev* sys, int nsys, int32_t* iters, double* relres, int32_t* status) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nsys) return;

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
   __shared__ double red[NT / 32];
   __shared__ double bcast;
   __shared__ int s_last;
-  __shared__ C zring[4][3];  // stretch coefficients (s_z, 1/(s_z(k-1/2) h^2), 1/(s_z(k+1/2) h^2)) per plane
+  __shared__ int s_abort;
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   C* Fbase = reinterpret_cast<C*>(smem + (size_t)S * L::STAGE);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::STAGE + L::FRING);
@@ -134,21 +134,27 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
     if (tid == 0) atomicExch(T.err, 2);
     return;
   }
-  // this thread's halo-ring element (fixed for the whole kernel)
-  const bool has_ring = tid < RING;
+  // this thread's halo-ring element (fixed for the whole kernel); the RING elements are
+  // dealt round-robin over the warps so every warp carries the same share
+  constexpr int NW = NT / 32;
+  static_assert((RING + NW - 1) / NW <= 32, "ring share fits a warp");
+  const int r_e = (tid & 31) * NW + (tid >> 5);
+  const bool has_ring = r_e < RING;
   int r_si = 0, r_sj = 0;
-  if (tid < WRI_TX) { r_si = tid + 1; r_sj = 0; }
-  else if (tid < 2 * WRI_TX) { r_si = tid - WRI_TX + 1; r_sj = BY + 1; }
-  else if (tid < 2 * WRI_TX + BY) { r_si = 0; r_sj = tid - 2 * WRI_TX + 1; }
-  else { r_si = WRI_TX + 1; r_sj = tid - 2 * WRI_TX - BY + 1; }
+  if (r_e < WRI_TX) { r_si = r_e + 1; r_sj = 0; }
+  else if (r_e < 2 * WRI_TX) { r_si = r_e - WRI_TX + 1; r_sj = BY + 1; }
+  else if (r_e < 2 * WRI_TX + BY) { r_si = 0; r_sj = r_e - 2 * WRI_TX + 1; }
+  else { r_si = WRI_TX + 1; r_sj = r_e - 2 * WRI_TX - BY + 1; }
   const int r_raw = r_sj * L::HW + r_si + 1;   // element in a halo box
   const int r_f = r_sj * L::FW + r_si;         // element in an F plane
   const int o_raw = (ty + 1) * L::HW + tx + 2;  // own node in a halo box
   const int o_f = (ty + 1) * L::FW + tx + 1;    // own node in an F plane
   const int o_ctr = ty * WRI_TX + tx;           // own node in a 32 x BY box
 
-  if (tid == 0)
+  if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    s_abort = 0;
+  }
   __syncthreads();
   unsigned uses = 0;  // stage uses so far (uniform across the CTA)
 
@@ -232,7 +238,7 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
           (x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi) && (y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi);
       const float om2 = G.om2f;
       const float ih2 = G.ih2f;
-      const AxisPml az = G.az;
+      const float2* ztab = G.ztab + (CONJ ? 3 * nz : 0);
 
       __syncthreads();  // the previous item no longer reads the stages, the F ring or zring
       if (tid == 0)
@@ -246,11 +252,9 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
       for (int q = 0; q < count; ++q, po += plane) {
         const int st = (int)((uses + q) % S);
         const uint32_t par = ((uses + q) / S) & 1u;
-        const bool ok = mbar_wait(&bar[st], par);
-        if (__syncthreads_or(!ok)) {
-          q_fail = q;
-          break;
-        }
+        // every thread waits for the stage itself; a time-out is made uniform at the
+        // plane barrier below (the F values of a failed plane are never used)
+        if (!mbar_wait(&bar[st], par)) s_abort = 1;
         const unsigned char* base = smem + (size_t)st * L::STAGE;
         const C* A = reinterpret_cast<const C*>(base);
         const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
@@ -274,14 +278,11 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
         const float m_new = MT[o_ctr];
         // F on this thread's halo-ring element (zeros outside the grid come from the copies)
         if (has_ring) Fq[r_f] = hasB ? A[r_raw] + coef * B[r_raw] : A[r_raw];
-        // z coefficients of plane kq, used by the stencil of the next iteration
-        if (tid == 32) {
-          const float ih2z = ih2;
-          zring[q & 3][0] = stretch_at<float, CONJ>(az, float(kq));
-          zring[q & 3][1] = ih2z * inv(stretch_at<float, CONJ>(az, float(kq) - 0.5f));
-          zring[q & 3][2] = ih2z * inv(stretch_at<float, CONJ>(az, float(kq) + 0.5f));
-        }
         __syncthreads();
+        if (s_abort) {
+          q_fail = q;
+          break;
+        }
         if (tid == 0 && issued < count) {
           issue(issued);
           ++issued;
@@ -303,10 +304,10 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
             AF = stencil_interior<float>(ih2, om2m, u, uxm, uxp, uym, uyp, uzm, uzp);
           } else {
             ZCoef<float> zc;
-            const C* zr = zring[(q - 1) & 3];
-            zc.sz = zr[0];
-            zc.izm = zr[1];
-            zc.izp = zr[2];
+            const C* zr = ztab + 3 * kp;
+            zc.sz = __ldg(zr);
+            zc.izm = __ldg(zr + 1);
+            zc.izp = __ldg(zr + 2);
             AF = stencil_general<float, CONJ>(G, cxy, zc, om2m, u, uxm, uxp, uym, uyp, uzm, uzp);
           }
           if (own) {
