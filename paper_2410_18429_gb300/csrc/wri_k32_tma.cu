@@ -31,10 +31,38 @@ static cudaError_t launch_one(const Batch& b, const TmaSet& T, int grid, cudaStr
   return cudaGetLastError();
 }
 
-int tma_config_count() { return 4; }
+template <int MODE, int BY, int S>
+static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
+  static int occ = -1;
+  const size_t smem = TmaLayout2<MODE, BY>::bytes(S);
+  auto kern = k_phase_tma2<MODE, BY, S, (BY <= 8 ? 4 : 2)>;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 16 * BY, smem);
+    if (e != cudaSuccess) return e;
+    occ = n > 0 ? n : 1;
+  }
+  if (grid <= 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long g = (long long)sms * occ;
+    grid = (int)(g < b.nitems ? g : b.nitems);
+    if (grid < 1) grid = 1;
+  }
+  kern<<<grid, dim3(16, BY), smem, st>>>(b, T);
+  return cudaGetLastError();
+}
 
-// config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4)
-int tma_config_by(int cfg) { return cfg >= 2 ? 16 : 8; }
+int tma_config_count() { return 7; }
+
+// config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4) with one node per thread;
+// 4 -> (16, 4), 5 -> (16, 3), 6 -> (8, 6) with two x-adjacent nodes per thread
+int tma_config_by(int cfg) { return (cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5) ? 16 : 8; }
 
 cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   if (b.nitems <= 0) return cudaSuccess;
@@ -49,6 +77,15 @@ cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T,
   WRI_TMA_CASE(M_P1, 3, 16, 4)
   WRI_TMA_CASE(M_P2, 3, 16, 4)
 #undef WRI_TMA_CASE
+#define WRI_TMA2_CASE(M, C_, BY_, S_) \
+  if (mode == M && cfg == C_) return launch_two<M, BY_, S_>(b, T, grid, st);
+  WRI_TMA2_CASE(M_P1, 4, 16, 4)
+  WRI_TMA2_CASE(M_P2, 4, 16, 4)
+  WRI_TMA2_CASE(M_P1, 5, 16, 3)
+  WRI_TMA2_CASE(M_P2, 5, 16, 3)
+  WRI_TMA2_CASE(M_P1, 6, 8, 6)
+  WRI_TMA2_CASE(M_P2, 6, 8, 6)
+#undef WRI_TMA2_CASE
   return cudaErrorInvalidValue;
 }
 

@@ -36,8 +36,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);
-  const int lane = threadIdx.x & 31;
-  const int wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  const int ltid = threadIdx.y * blockDim.x + threadIdx.x;  // any block shape
+  const int lane = ltid & 31;
+  const int wid = ltid >> 5;
   __syncthreads();
   if (lane == 0) red[wid] = v;
   __syncthreads();

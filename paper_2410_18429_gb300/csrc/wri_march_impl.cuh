@@ -16,13 +16,13 @@ __device__ __forceinline__ cx<R> ldg_c(const cx<R>* p) {
 
 // ------------------------------------------------------------------ finalizers
 // Run by every thread of the CTA that completed the last tile of system `sd`.
-template <typename R, typename OR, int MODE, int BY>
+// NT is the number of threads of the CTA (any 2-D shape).
+template <typename R, typename OR, int MODE, int NT>
 __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, bool xonly, double* red,
                          double* bcast) {
   typedef cx<R> C;
   typedef cx<OR> OC;
-  constexpr int NT = WRI_TX * BY;
-  const int tid = threadIdx.y * WRI_TX + threadIdx.x;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   __threadfence();
   const long long off = (long long)sl * G.n;
   const int cur = sd->iter & 1;
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
       s_last = (t == (unsigned)(G.ntiles - 1));
     }
     __syncthreads();
-    if (s_last) finalize<R, OR, MODE, BY>(b, G, sd, sl0, xonly, red, &bcast);
+    if (s_last) finalize<R, OR, MODE, WRI_TX * BY>(b, G, sd, sl0, xonly, red, &bcast);
   }
 }
 

@@ -342,7 +342,291 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
       s_last = (t == (unsigned)(G.ntiles - 1));
     }
     __syncthreads();
-    if (s_last) finalize<float, float, MODE, BY>(b, G, sd, sl, xonly, red, &bcast);
+    if (s_last) finalize<float, float, MODE, NT>(b, G, sd, sl, xonly, red, &bcast);
+  }
+}
+
+// ------------------------------------------------------------------ two nodes per thread
+// Same pipeline as k_phase_tma, with every thread owning the two x-adjacent nodes
+// (x0 + 2 tx, x0 + 2 tx + 1) of row y0 + ty: shared-memory and global accesses move 16
+// bytes per instruction and the per-plane control, barrier and address work is paid once
+// per pair.  F planes use the copy boxes' 36-column layout so pairs stay 16-byte aligned.
+template <int MODE, int BY>
+struct TmaLayout2 {
+  static constexpr int HW = WRI_TX + 4;  // 36 columns: x0-2 .. x0+33 (boxes and F planes)
+  static constexpr int HH = BY + 2;
+  static constexpr int pad(int v) { return (v + 127) / 128 * 128; }
+  static constexpr int HALO = HW * HH * 8;
+  static constexpr int CTR = WRI_TX * BY * 8;
+  static constexpr int MB = WRI_TX * BY * 4;
+  static constexpr int OFF_B = pad(HALO);
+  static constexpr int OFF_X = OFF_B + pad(HALO);
+  static constexpr int OFF_M = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);
+  static constexpr int STAGE = OFF_M + pad(MB);
+  static constexpr int FPL = HH * HW;  // complex elements of one F plane
+  static constexpr int FRING = 4 * FPL * 8;
+  static size_t bytes(int S) { return 128 + (size_t)S * STAGE + FRING + 8 * S; }
+};
+
+__device__ __forceinline__ float4 ld4(const float2* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+template <int MODE, int BY, int S, int MINB>
+__global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_constant__ Batch b,
+                                                              const __grid_constant__ TmaSet T) {
+  static_assert(MODE == M_P1 || MODE == M_P2, "TMA path covers the two CGLS phases");
+  typedef float2 C;
+  typedef TmaLayout2<MODE, BY> L;
+  constexpr bool CONJ = (MODE == M_P2);
+  constexpr int NT = 16 * BY;
+  constexpr int NW = NT / 32;
+  constexpr int RW = 32 + 2 * BY;  // ring work items: 2 x 16 pairs (y halo rows) + 2 x BY singles (x halo)
+  static_assert(NT % 32 == 0 && (RW + NW - 1) / NW <= 32, "ring share fits a warp");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red[NT / 32];
+  __shared__ double bcast;
+  __shared__ int s_last;
+  __shared__ int s_abort;
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  C* Fbase = reinterpret_cast<C*>(smem + (size_t)S * L::STAGE);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::STAGE + L::FRING);
+
+  const int tx = threadIdx.x, ty = threadIdx.y;  // tx in [0, 16)
+  const int tid = ty * 16 + tx;
+  if ((smem_addr(smem) & 127u) != 0u || (L::OFF_B & 127) || (L::OFF_X & 127) || (L::OFF_M & 127) ||
+      (L::STAGE & 127)) {
+    if (tid == 0) atomicExch(T.err, 2);
+    return;
+  }
+  // ring work item of this thread, dealt round-robin over warps
+  const int r_e = (tid & 31) * NW + (tid >> 5);
+  const bool has_ring = r_e < RW;
+  const bool r_pair = r_e < 32;
+  int r_idx;  // element index in a box / F plane (both 36 wide)
+  if (r_e < 16) r_idx = 2 * r_e + 2;                                  // row 0, pair
+  else if (r_e < 32) r_idx = (BY + 1) * L::HW + 2 * (r_e - 16) + 2;  // row BY+1, pair
+  else if (r_e < 32 + BY) r_idx = (r_e - 32 + 1) * L::HW + 1;        // column x0-1
+  else r_idx = (r_e - 32 - BY + 1) * L::HW + 34;                     // column x0+32
+  const int o = (ty + 1) * L::HW + 2 * tx + 2;  // own pair in a box / F plane
+  const int oc = ty * WRI_TX + 2 * tx;          // own pair in a 32 x BY box
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    s_abort = 0;
+  }
+  __syncthreads();
+  unsigned uses = 0;
+
+  for (long long item = blockIdx.x; item < b.nitems; item += gridDim.x) {
+    const int gi = find_group(b, item);
+    const GroupDev& G = b.g[gi];
+    const long long local = item - G.item0;
+    const int sl = (int)(local % G.nsys);
+    const int tile = (int)(local / G.nsys);
+    SysDev* sd = b.sys + (G.sys0 + sl);
+    const int state = sd->state;
+    if (MODE == M_P1 ? (state == ST_DONE) : (state != ST_ACTIVE)) continue;
+    const bool xonly = (MODE == M_P1 && state == ST_FINISHING);
+
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int tzi = tile % G.zsplit;
+    const int txy = tile / G.zsplit;
+    const int x0 = (txy % G.tiles_x) * WRI_TX;
+    const int y0 = (txy / G.tiles_x) * BY;
+    const int z0 = tzi * G.zc;
+    const int z1 = min(z0 + G.zc, nz);
+    const int i0 = x0 + 2 * tx, j = y0 + ty;
+    const bool own = (i0 < nx) && (j < ny);  // nx is even: the pair is in or out as a whole
+    const long long plane = (long long)nx * ny;
+    const long long col = (long long)j * nx + i0;
+    const long long off = (long long)sl * G.n;
+    const int iter = sd->iter;
+    const int cur = iter & 1;
+    double accd = 0.0;
+
+    if (xonly) {
+      C* X = (C*)G.x + off + col;
+      const C* Pc = (const C*)G.p[cur] + off + col;
+      const float a = (float)sd->alpha;
+      if (own)
+        for (int k = z0; k < z1; ++k) {
+          const long long q = k * plane;
+          const float4 xv = ld4(X + q), pv = __ldg(reinterpret_cast<const float4*>(Pc + q));
+          st4(X + q, lo2(xv) + a * lo2(pv), hi2(xv) + a * hi2(pv));
+        }
+    } else {
+      const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
+      const bool hasB = (MODE == M_P2) || iter > 0;
+      const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
+      const bool hasX = (MODE == M_P1) && iter > 0;
+      const CUtensorMap* mapX = &T.map[gi][TM_X];
+      const CUtensorMap* mapM = &T.map[gi][TM_M];
+      const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + L::MB;
+      const float coef = (MODE == M_P1) ? (float)sd->beta : -(float)sd->alpha;
+      const float xal = (float)sd->alpha;
+      C* pF = ((MODE == M_P1) ? (C*)G.p[cur ^ 1] : (C*)G.r1[cur ^ 1]) + off + col;
+      C* pX = (C*)G.x + off + col;
+      C* pO = ((MODE == M_P1) ? (C*)G.t1 : (C*)G.s) + off + col;
+      int src_k = -1;
+      long long src_col = -1;
+      if (MODE == M_P1 && G.masked) {
+        src_k = (int)(sd->src / plane);
+        src_col = sd->src - (long long)src_k * plane;
+      }
+      const int src_lane = (src_col == col) ? 0 : (src_col == col + 1) ? 1 : -1;
+      const int count = z1 - z0 + 2;
+
+      auto issue = [&](int q) {
+        const int st = (int)((uses + q) % S);
+        unsigned char* base = smem + (size_t)st * L::STAGE;
+        const int kq = z0 - 1 + q;
+        mbar_expect_tx(&bar[st], tx_bytes);
+        tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &bar[st]);
+        if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &bar[st]);
+        if (hasX) tma_load_4d(base + L::OFF_X, mapX, x0, y0, kq, sl, &bar[st]);
+        tma_load_3d(base + L::OFF_M, mapM, x0, y0, kq, &bar[st]);
+      };
+
+      int xlo, xhi, ylo, yhi, zlo, zhi;
+      interior_range(G.ax, xlo, xhi);
+      interior_range(G.ay, ylo, yhi);
+      interior_range(G.az, zlo, zhi);
+      const bool xy_int =
+          (x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi) && (y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi);
+      XYCoef<float> c0, c1;
+      if (!xy_int) {
+        c0 = xy_coef<float, CONJ>(G, min(i0, nx - 1), min(j, ny - 1));
+        c1 = xy_coef<float, CONJ>(G, min(i0 + 1, nx - 1), min(j, ny - 1));
+      }
+      const float om2 = G.om2f;
+      const float ih2 = G.ih2f;
+      const float2* ztab = G.ztab + (CONJ ? 3 * nz : 0);
+
+      __syncthreads();
+      if (tid == 0)
+        for (int q = 0; q < S && q < count; ++q) issue(q);
+
+      CompSum acc;
+      float2 m_prev = make_float2(0.f, 0.f);
+      int issued = min(S, count);
+      int q_fail = -1;
+      long long po = (long long)(z0 - 1) * plane;
+      for (int q = 0; q < count; ++q, po += plane) {
+        const int st = (int)((uses + q) % S);
+        const uint32_t par = ((uses + q) / S) & 1u;
+        if (!mbar_wait(&bar[st], par)) s_abort = 1;
+        const unsigned char* base = smem + (size_t)st * L::STAGE;
+        const C* A = reinterpret_cast<const C*>(base);
+        const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
+        const C* XT = reinterpret_cast<const C*>(base + L::OFF_X);
+        const float* MT = reinterpret_cast<const float*>(base + L::OFF_M);
+        const int kq = z0 - 1 + q;
+        C* Fq = Fbase + (q & 3) * L::FPL;
+        const bool mine = own && kq >= z0 && kq < z1;
+        {
+          const float4 a = ld4(A + o);
+          C v0 = lo2(a), v1 = hi2(a);
+          if (hasB) {
+            const float4 bb = ld4(B + o);
+            v0 = v0 + coef * lo2(bb);
+            v1 = v1 + coef * hi2(bb);
+            if (MODE == M_P1 && mine) {
+              const float4 xv = ld4(XT + oc);
+              st4(pX + po, lo2(xv) + xal * lo2(bb), hi2(xv) + xal * hi2(bb));
+            }
+          }
+          st4(Fq + o, v0, v1);
+          if (mine) st4(pF + po, v0, v1);
+        }
+        const float2 m_new = *reinterpret_cast<const float2*>(MT + oc);
+        if (has_ring) {
+          if (r_pair) {
+            const float4 a = ld4(A + r_idx);
+            if (hasB) {
+              const float4 bb = ld4(B + r_idx);
+              st4(Fq + r_idx, lo2(a) + coef * lo2(bb), hi2(a) + coef * hi2(bb));
+            } else {
+              st4(Fq + r_idx, lo2(a), hi2(a));
+            }
+          } else {
+            Fq[r_idx] = hasB ? A[r_idx] + coef * B[r_idx] : A[r_idx];
+          }
+        }
+        __syncthreads();
+        if (s_abort) {
+          q_fail = q;
+          break;
+        }
+        if (tid == 0 && issued < count) {
+          issue(issued);
+          ++issued;
+        }
+        if (q >= 2) {
+          const int kp = kq - 1;
+          const C* Fm = Fbase + ((q - 2) & 3) * L::FPL;
+          const C* Fc = Fbase + ((q - 1) & 3) * L::FPL;
+          const float4 U = ld4(Fc + o);
+          const C u0 = lo2(U), u1 = hi2(U);
+          const C l = Fc[o - 1], r = Fc[o + 2];
+          const float4 YM = ld4(Fc + o - L::HW), YP = ld4(Fc + o + L::HW);
+          const float4 ZM = ld4(Fm + o), ZP = ld4(Fq + o);
+          C a0, a1;
+          if (xy_int && kp >= zlo && kp <= zhi) {
+            a0 = stencil_interior<float>(ih2, om2 * m_prev.x, u0, l, u1, lo2(YM), lo2(YP), lo2(ZM), lo2(ZP));
+            a1 = stencil_interior<float>(ih2, om2 * m_prev.y, u1, u0, r, hi2(YM), hi2(YP), hi2(ZM), hi2(ZP));
+          } else {
+            ZCoef<float> zc;
+            const C* zr = ztab + 3 * kp;
+            zc.sz = __ldg(zr);
+            zc.izm = __ldg(zr + 1);
+            zc.izp = __ldg(zr + 2);
+            if (xy_int) {
+              c0 = xy_coef<float, CONJ>(G, i0, j);  // interior column: unit stretch, cheap
+              c1 = c0;
+            }
+            a0 = stencil_general<float, CONJ>(G, c0, zc, om2 * m_prev.x, u0, l, u1, lo2(YM), lo2(YP), lo2(ZM),
+                                              lo2(ZP));
+            a1 = stencil_general<float, CONJ>(G, c1, zc, om2 * m_prev.y, u1, u0, r, hi2(YM), hi2(YP), hi2(ZM),
+                                              hi2(ZP));
+          }
+          if (own) {
+            if (MODE == M_P1 && kp == src_k) {
+              if (src_lane == 0) a0 = czero<float>();
+              if (src_lane == 1) a1 = czero<float>();
+            }
+            st4(pO + po - plane, a0, a1);
+            acc.add(abs2(a0));
+            acc.add(abs2(a1));
+          }
+        }
+        m_prev = m_new;
+      }
+      if (q_fail >= 0) {
+        if (tid == 0) {
+          atomicExch(T.err, 1);
+          for (int qq = q_fail; qq < issued; ++qq) mbar_wait(&bar[(uses + qq) % S], ((uses + qq) / S) & 1u);
+        }
+        __syncthreads();
+        return;
+      }
+      uses += (unsigned)count;
+      accd = acc.value();
+    }
+
+    const double tsum = block_sum<NT>(accd, red);
+    if (tid == 0 && !xonly) b.partial[sd->part_off + tile] = tsum;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned t = atomicAdd(&sd->ticket, 1u);
+      s_last = (t == (unsigned)(G.ntiles - 1));
+    }
+    __syncthreads();
+    if (s_last) finalize<float, float, MODE, NT>(b, G, sd, sl, xonly, red, &bcast);
   }
 }
 
