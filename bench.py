@@ -42,6 +42,10 @@ def parse():
                    help="keep only one frequency group (0: 3 Hz, 1: 5 Hz, 2: 8 Hz); profiling cases")
     p.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU legs")
     p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 z-march only, 2+c TMA configuration c")
+    p.add_argument("--order", type=int, default=0,
+                   help="TMA work order: 0 auto, 1 system-major, 2 tile-major, 3 z-chunk-major")
+    p.add_argument("--zsplit", type=int, default=0, help="z-chunks per tile column (0 = library choice)")
+    p.add_argument("--promo", type=int, default=0, help="TMA L2 promotion: 0 auto, 1 none, 2 64B, 3 128B, 4 256B")
     return p.parse_args()
 
 
@@ -180,7 +184,8 @@ def main():
     nsys = sum(g.nsys for g in groups)
     n_nodes = [g.spec.n for g in groups]
     K = 2
-    opts = wri.make_opts(tol=0.0, max_iter=args.iters, dtype=wri.C64, poll_every=K, kernel=args.kernel)
+    opts = wri.make_opts(tol=0.0, max_iter=args.iters, dtype=wri.C64, poll_every=K, kernel=args.kernel, order=args.order,
+                         zsplit=args.zsplit, l2_promotion=args.promo)
     wsz = wri.workspace_size(specs, opts)
     work = torch.empty(wsz, dtype=torch.uint8, device=dev)
     grads = [torch.zeros(g.spec.nz, g.spec.ny, g.spec.nx, dtype=torch.float64, device=dev) for g in groups]
@@ -231,7 +236,8 @@ def main():
 
     # ---- roofline of the fused CG iteration (phase 1 + phase 2 kernels), live with CUDA events
     def timed_solve(iters):
-        o = wri.make_opts(tol=0.0, max_iter=iters, dtype=wri.C64, poll_every=K, kernel=args.kernel)
+        o = wri.make_opts(tol=0.0, max_iter=iters, dtype=wri.C64, poll_every=K, kernel=args.kernel, order=args.order,
+                         zsplit=args.zsplit, l2_promotion=args.promo)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)

@@ -111,7 +111,12 @@ typedef struct {
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
   int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
-                          1 = z-march kernels only, 2 + c = TMA configuration c (0..3) */
+                          1 = z-march kernels only, 2 + c = TMA configuration c (0..8) */
+  int32_t order;       /* TMA phases: 0 = automatic, 1 = tiles of a system consecutive,
+                          2 = systems of a tile consecutive, 3 = z-chunk slowest,
+                          4 / 5 / 6 = blocks of 4 / 8 / 16 systems, tiles in order */
+  int32_t l2_promotion; /* TMA copies: L2 fill size on a miss, 0 = automatic, 1 = none,
+                           2 = 64 B, 3 = 128 B, 4 = 256 B */
 } wri_solve_opts;
 
 /* y = A x (wri_apply_A) or y = A^H x (wri_apply_AH) for `nsys` vectors that share the

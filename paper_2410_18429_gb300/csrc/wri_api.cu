@@ -21,6 +21,13 @@ using namespace wri;
 namespace {
 
 constexpr int kRefSMs = 152;  // SMs of a GB300; sets the z-split of small batches
+// Measured defaults of the TMA phases on GB300 (128 sources x 3 frequency grids):
+// two nodes per thread, 32 x 8 tiles, 4 stages, 4 CTAs/SM; work items in blocks of
+// 16 systems (neighbouring tiles of a system run together, so their halos meet in L2);
+// L2 fills of 64 bytes on a copy miss (128-byte fills over-fetch the halo columns).
+constexpr int kDefaultTmaCfg = 8;
+constexpr int kDefaultOrder = 6;
+constexpr int kDefaultPromotion = 2;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -179,7 +186,7 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
     for (int gi = 0; gi < ngroups; ++gi)
       ok = ok && (groups[gi].grid.nx % 4 == 0) && ((uintptr_t)groups[gi].u % 16 == 0);
     if (ok) {
-      P.tma_cfg = o->kernel >= 2 ? o->kernel - 2 : 0;
+      P.tma_cfg = o->kernel >= 2 ? o->kernel - 2 : kDefaultTmaCfg;
       P.by = tma_config_by(P.tma_cfg);
     }
   }
@@ -246,6 +253,8 @@ int validate_opts(const wri_solve_opts* o) {
   if (!(o->tol >= 0) || !std::isfinite(o->tol) || o->max_iter < 1) return WRI_EINVAL;
   if (o->max_refine < 0 || o->poll_every < 0 || o->tile < 0 || o->tile > 3 || o->zsplit < 0) return WRI_EINVAL;
   if (o->kernel < 0 || o->kernel > 1 + tma_config_count()) return WRI_EINVAL;
+  if (o->order < 0 || o->order > 6) return WRI_EINVAL;
+  if (o->l2_promotion < 0 || o->l2_promotion > 4) return WRI_EINVAL;
   if (o->max_refine > 0) {
     if (o->dtype != WRI_C64) return WRI_ENOTSUP;
     if (!(o->refine_tol >= 0) || !(o->inner_tol > 0 && o->inner_tol < 1)) return WRI_EINVAL;
@@ -376,38 +385,49 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 4-D map over [nsys][nz][ny][nx] complex64 vectors (8-byte elements); box bx x by x 1 x 1
-bool encode_vec(CUtensorMap* m, const void* base, const GroupDev& G, int bx, int by) {
+CUtensorMapL2promotion promo_of(int p) {
+  switch (p) {
+    case 1: return CU_TENSOR_MAP_L2_PROMOTION_NONE;
+    case 2: return CU_TENSOR_MAP_L2_PROMOTION_L2_64B;
+    case 3: return CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+    case 4: return CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+  }
+  return CU_TENSOR_MAP_L2_PROMOTION_NONE;
+}
+
+bool encode_vec(CUtensorMap* m, const void* base, const GroupDev& G, int bx, int by, int promo) {
   const cuuint64_t dims[4] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz, (cuuint64_t)G.nsys};
   const cuuint64_t strides[3] = {(cuuint64_t)G.nx * 8, (cuuint64_t)G.nx * G.ny * 8, (cuuint64_t)G.n * 8};
   const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(base), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo_of(promo),
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // 3-D map over the float model [nz][ny][nx]; box 32 x by x 1
-bool encode_model(CUtensorMap* m, const void* base, const GroupDev& G, int by) {
+bool encode_model(CUtensorMap* m, const void* base, const GroupDev& G, int by, int promo) {
   const cuuint64_t dims[3] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz};
   const cuuint64_t strides[2] = {(cuuint64_t)G.nx * 4, (cuuint64_t)G.nx * G.ny * 4};
   const cuuint32_t box[3] = {WRI_TX, (cuuint32_t)by, 1};
   const cuuint32_t es[3] = {1, 1, 1};
   return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo_of(promo),
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool build_tma(const Batch& b, const Plan& P, int* err, TmaSet& T) {
+bool build_tma(const Batch& b, const Plan& P, int* err, int promo, TmaSet& T) {
   if (!encode_fn()) return false;
   std::memset(&T, 0, sizeof(T));
   T.err = err;
-  const int hw = WRI_TX + 4, hh = P.by + 2;
+  const int hw = WRI_TX + 4, hh = P.by + 2, pr = promo;
   for (int gi = 0; gi < b.ngroups; ++gi) {
     const GroupDev& G = b.g[gi];
-    bool ok = encode_vec(&T.map[gi][TM_S], G.s, G, hw, hh) && encode_vec(&T.map[gi][TM_P0], G.p[0], G, hw, hh) &&
-              encode_vec(&T.map[gi][TM_P1], G.p[1], G, hw, hh) && encode_vec(&T.map[gi][TM_X], G.x, G, WRI_TX, P.by) &&
-              encode_vec(&T.map[gi][TM_T1], G.t1, G, hw, hh) && encode_vec(&T.map[gi][TM_R0], G.r1[0], G, hw, hh) &&
-              encode_vec(&T.map[gi][TM_R1], G.r1[1], G, hw, hh) && encode_model(&T.map[gi][TM_M], G.m, G, P.by);
+    bool ok = encode_vec(&T.map[gi][TM_S], G.s, G, hw, hh, pr) && encode_vec(&T.map[gi][TM_P0], G.p[0], G, hw, hh, pr) &&
+              encode_vec(&T.map[gi][TM_P1], G.p[1], G, hw, hh, pr) &&
+              encode_vec(&T.map[gi][TM_X], G.x, G, WRI_TX, P.by, pr) && encode_vec(&T.map[gi][TM_T1], G.t1, G, hw, hh, pr) &&
+              encode_vec(&T.map[gi][TM_R0], G.r1[0], G, hw, hh, pr) && encode_vec(&T.map[gi][TM_R1], G.r1[1], G, hw, hh, pr) &&
+              encode_model(&T.map[gi][TM_M], G.m, G, P.by, pr);
     if (!ok) return false;
   }
   return true;
@@ -514,11 +534,14 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   }
   Batch b1 = b, b2 = b;
   b1.flavor = b2.flavor = 0;
+  const int ord = o->order ? o->order : kDefaultOrder;
+  b1.order = b2.order = (ord == 1) ? 1 : (ord == 3) ? 2 : (ord >= 4) ? 3 : 0;
+  b1.sblock = b2.sblock = (ord >= 4) ? (1 << (ord - 2)) : 1;  // 4 -> 4 systems, 5 -> 8, 6 -> 16
   const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
   if (P.tma_cfg >= 0) {
     WRI_CK(launch_ztable(b, st));
     static thread_local TmaSet T;  // ~8 KB: kept off the stack
-    if (build_tma(b, P, b.remaining + 1, T))
+    if (build_tma(b, P, b.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, T))
       return run_loop(P, b1, b2, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, &T);
     // descriptors rejected (e.g. an unaligned model array): same decomposition, z-march kernels
   }

@@ -166,11 +166,42 @@ struct Batch {
   int max_iter;
   int flavor;           // kernel-specific sub-mode
   int cgnr;             // 1: inner solve on the normal equations (no data-space residual)
+  int order;            // TMA phases: work-item order, 0 = systems fastest, 1 = tiles of a system
+                        // consecutive, 2 = z-chunk slowest (the resident wave shares z-slabs),
+                        // 3 = blocks of sblock systems, tiles in order, systems fastest in a block
+  int sblock;           // systems per block of order 3
   double tol;           // tolerance of a cold-start solve
   double refine_tol, inner_tol;
   int outer, max_refine, warm;
   GroupDev g[WRI_MAXG];
 };
+
+// (system, tile) of a work item of group G under the batch's work order
+__device__ __forceinline__ void item_coords(const Batch& b, const GroupDev& G, long long local, int& sl, int& tile) {
+  if (b.order == 1) {
+    sl = (int)(local / G.ntiles);
+    tile = (int)(local % G.ntiles);
+  } else if (b.order == 2) {
+    const int nxy = G.tiles_x * G.tiles_y;
+    const long long per_z = (long long)G.nsys * nxy;
+    const int tz = (int)(local / per_z);
+    const long long rem = local - (long long)tz * per_z;
+    sl = (int)(rem / nxy);
+    tile = (int)(rem % nxy) * G.zsplit + tz;
+  } else if (b.order == 3) {
+    const int sb = min(b.sblock, G.nsys);
+    const int nb = (G.nsys + sb - 1) / sb;
+    const long long per_block = (long long)sb * G.ntiles;
+    const int blk = (int)min(local / per_block, (long long)(nb - 1));
+    const long long rem = local - (long long)blk * per_block;
+    const int cnt = min(sb, G.nsys - blk * sb);
+    tile = (int)(rem / cnt);
+    sl = blk * sb + (int)(rem % cnt);
+  } else {
+    sl = (int)(local % G.nsys);
+    tile = (int)(local / G.nsys);
+  }
+}
 
 __device__ __forceinline__ int find_group(const Batch& b, long long item) {
   int g = 0;

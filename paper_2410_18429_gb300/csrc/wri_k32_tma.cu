@@ -31,11 +31,11 @@ static cudaError_t launch_one(const Batch& b, const TmaSet& T, int grid, cudaStr
   return cudaGetLastError();
 }
 
-template <int MODE, int BY, int S>
+template <int MODE, int BY, int S, int MINB>
 static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   static int occ = -1;
   const size_t smem = TmaLayout2<MODE, BY>::bytes(S);
-  auto kern = k_phase_tma2<MODE, BY, S, (BY <= 8 ? 4 : 2)>;
+  auto kern = k_phase_tma2<MODE, BY, S, MINB>;
   if (occ < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -58,10 +58,11 @@ static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStr
   return cudaGetLastError();
 }
 
-int tma_config_count() { return 7; }
+int tma_config_count() { return 9; }
 
 // config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4) with one node per thread;
-// 4 -> (16, 4), 5 -> (16, 3), 6 -> (8, 6) with two x-adjacent nodes per thread
+// 4 -> (16, 4), 5 -> (16, 3), 6 -> (8, 6), 7 -> (8, 3; 5 CTAs/SM), 8 -> (8, 4; 4 CTAs/SM) with two
+// x-adjacent nodes per thread
 int tma_config_by(int cfg) { return (cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5) ? 16 : 8; }
 
 cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
@@ -77,14 +78,18 @@ cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T,
   WRI_TMA_CASE(M_P1, 3, 16, 4)
   WRI_TMA_CASE(M_P2, 3, 16, 4)
 #undef WRI_TMA_CASE
-#define WRI_TMA2_CASE(M, C_, BY_, S_) \
-  if (mode == M && cfg == C_) return launch_two<M, BY_, S_>(b, T, grid, st);
-  WRI_TMA2_CASE(M_P1, 4, 16, 4)
-  WRI_TMA2_CASE(M_P2, 4, 16, 4)
-  WRI_TMA2_CASE(M_P1, 5, 16, 3)
-  WRI_TMA2_CASE(M_P2, 5, 16, 3)
-  WRI_TMA2_CASE(M_P1, 6, 8, 6)
-  WRI_TMA2_CASE(M_P2, 6, 8, 6)
+#define WRI_TMA2_CASE(M, C_, BY_, S_, MB_) \
+  if (mode == M && cfg == C_) return launch_two<M, BY_, S_, MB_>(b, T, grid, st);
+  WRI_TMA2_CASE(M_P1, 4, 16, 4, 2)
+  WRI_TMA2_CASE(M_P2, 4, 16, 4, 2)
+  WRI_TMA2_CASE(M_P1, 5, 16, 3, 2)
+  WRI_TMA2_CASE(M_P2, 5, 16, 3, 2)
+  WRI_TMA2_CASE(M_P1, 6, 8, 6, 3)
+  WRI_TMA2_CASE(M_P2, 6, 8, 6, 3)
+  WRI_TMA2_CASE(M_P1, 7, 8, 3, 5)
+  WRI_TMA2_CASE(M_P2, 7, 8, 3, 5)
+  WRI_TMA2_CASE(M_P1, 8, 8, 4, 4)
+  WRI_TMA2_CASE(M_P2, 8, 8, 4, 4)
 #undef WRI_TMA2_CASE
   return cudaErrorInvalidValue;
 }

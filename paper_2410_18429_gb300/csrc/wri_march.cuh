@@ -115,6 +115,33 @@ __device__ __forceinline__ cx<R> stencil_general(const GroupDev& G, const XYCoef
   return om2m * (w * u) + syz * lx + sxz * ly + c.sxy * lz;
 }
 
+// (A u) at one node when only the axes flagged XP, YP, ZP are stretched; the others have
+// s = 1 and real coefficients 1/h^2.  Same value as stencil_general, written as
+//   A u = s_z (s_y Lx + s_x Ly) + s_x s_y (Lz + omega^2 m s_z u),
+//   L_a = c_a(+1/2) (u_next - u) - c_a(-1/2) (u - u_prev),  c_a = 1/(s_a(half) h^2).
+template <bool XP, bool YP, bool ZP>
+__device__ __forceinline__ float2 stencil_axes(float ih2, float om2m, float2 u, float2 uxm, float2 uxp, float2 uym,
+                                               float2 uyp, float2 uzm, float2 uzp, float2 sx, float2 ixm,
+                                               float2 ixp, float2 sy, float2 iym, float2 iyp, float2 sz,
+                                               float2 izm, float2 izp) {
+  float2 lx, ly, lz;
+  if (XP) lx = ixp * (uxp - u) - ixm * (u - uxm);
+  else lx = ih2 * ((uxp + uxm) - 2.f * u);
+  if (YP) ly = iyp * (uyp - u) - iym * (u - uym);
+  else ly = ih2 * ((uyp + uym) - 2.f * u);
+  if (ZP) lz = izp * (uzp - u) - izm * (u - uzm);
+  else lz = ih2 * ((uzp + uzm) - 2.f * u);
+  const float2 a = (YP ? sy * lx : lx) + (XP ? sx * ly : ly);
+  const float2 zu = ZP ? sz * u : u;
+  const float2 b = lz + om2m * zu;
+  const float2 za = ZP ? sz * a : a;
+  float2 bb = b;
+  if (XP && YP) bb = (sx * sy) * b;
+  else if (XP) bb = sx * b;
+  else if (YP) bb = sy * b;
+  return za + bb;
+}
+
 // (A u) at one node in the interior (all stretch factors 1): omega^2 m u + Laplacian.
 template <typename R>
 __device__ __forceinline__ cx<R> stencil_interior(R ih2, R om2m, cx<R> u, cx<R> uxm, cx<R> uxp, cx<R> uym,

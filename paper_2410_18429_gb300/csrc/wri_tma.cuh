@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
     const int gi = find_group(b, item);
     const GroupDev& G = b.g[gi];
     const long long local = item - G.item0;
-    const int sl = (int)(local % G.nsys);
-    const int tile = (int)(local / G.nsys);
+    int sl, tile;
+    item_coords(b, G, local, sl, tile);
     SysDev* sd = b.sys + (G.sys0 + sl);
     const int state = sd->state;
     if (MODE == M_P1 ? (state == ST_DONE) : (state != ST_ACTIVE)) continue;
@@ -391,6 +391,9 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
   __shared__ double bcast;
   __shared__ int s_last;
   __shared__ int s_abort;
+  // x/y stretch coefficients of the current tile (general stencil only), rebuilt per item:
+  // node stretch s(i) and half-point 1/(s(i-1/2) h^2) for the 32 columns and BY rows
+  __shared__ C xs_tab[WRI_TX], xh_tab[WRI_TX + 1], ys_tab[BY], yh_tab[BY + 1];
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   C* Fbase = reinterpret_cast<C*>(smem + (size_t)S * L::STAGE);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::STAGE + L::FRING);
@@ -425,8 +428,8 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
     const int gi = find_group(b, item);
     const GroupDev& G = b.g[gi];
     const long long local = item - G.item0;
-    const int sl = (int)(local % G.nsys);
-    const int tile = (int)(local / G.nsys);
+    int sl, tile;
+    item_coords(b, G, local, sl, tile);
     SysDev* sd = b.sys + (G.sys0 + sl);
     const int state = sd->state;
     if (MODE == M_P1 ? (state == ST_DONE) : (state != ST_ACTIVE)) continue;
@@ -495,12 +498,26 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
       interior_range(G.ax, xlo, xhi);
       interior_range(G.ay, ylo, yhi);
       interior_range(G.az, zlo, zhi);
-      const bool xy_int =
-          (x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi) && (y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi);
-      XYCoef<float> c0, c1;
-      if (!xy_int) {
-        c0 = xy_coef<float, CONJ>(G, min(i0, nx - 1), min(j, ny - 1));
-        c1 = xy_coef<float, CONJ>(G, min(i0 + 1, nx - 1), min(j, ny - 1));
+      // which axes are stretched anywhere in this tile (uniform): selects the stencil variant
+      const int xpf = ((x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi)) ? 0 : 4;
+      const int ypf = ((y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi)) ? 0 : 2;
+      {
+        // coefficient tables of this tile (read only in the absorbing layer)
+        const float ih2t = G.ih2f;
+        for (int e = tid; e < 2 * WRI_TX + 2 * BY + 2; e += NT) {
+          if (e < WRI_TX) {
+            xs_tab[e] = stretch_at<float, CONJ>(G.ax, float(x0 + e));
+          } else if (e < 2 * WRI_TX + 1) {
+            const int c = e - WRI_TX;
+            xh_tab[c] = ih2t * inv(stretch_at<float, CONJ>(G.ax, float(x0 + c) - 0.5f));
+          } else if (e < 2 * WRI_TX + 1 + BY) {
+            const int r = e - 2 * WRI_TX - 1;
+            ys_tab[r] = stretch_at<float, CONJ>(G.ay, float(y0 + r));
+          } else {
+            const int r = e - 2 * WRI_TX - 1 - BY;
+            yh_tab[r] = ih2t * inv(stretch_at<float, CONJ>(G.ay, float(y0 + r) - 0.5f));
+          }
+        }
       }
       const float om2 = G.om2f;
       const float ih2 = G.ih2f;
@@ -575,23 +592,49 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
           const float4 YM = ld4(Fc + o - L::HW), YP = ld4(Fc + o + L::HW);
           const float4 ZM = ld4(Fm + o), ZP = ld4(Fq + o);
           C a0, a1;
-          if (xy_int && kp >= zlo && kp <= zhi) {
+          const int var = xpf | ypf | ((kp >= zlo && kp <= zhi) ? 0 : 1);
+          if (var == 0) {
             a0 = stencil_interior<float>(ih2, om2 * m_prev.x, u0, l, u1, lo2(YM), lo2(YP), lo2(ZM), lo2(ZP));
             a1 = stencil_interior<float>(ih2, om2 * m_prev.y, u1, u0, r, hi2(YM), hi2(YP), hi2(ZM), hi2(ZP));
           } else {
-            ZCoef<float> zc;
-            const C* zr = ztab + 3 * kp;
-            zc.sz = __ldg(zr);
-            zc.izm = __ldg(zr + 1);
-            zc.izp = __ldg(zr + 2);
-            if (xy_int) {
-              c0 = xy_coef<float, CONJ>(G, i0, j);  // interior column: unit stretch, cheap
-              c1 = c0;
+            // coefficients of the stretched axes only (tables of this tile / plane)
+            C sx0 = mkc(1.f, 0.f), sx1 = sx0, ixa = mkc(ih2, 0.f), ixb = ixa, ixc = ixa;
+            C sy = mkc(1.f, 0.f), iym = mkc(ih2, 0.f), iyp = iym;
+            C sz = mkc(1.f, 0.f), izm = mkc(ih2, 0.f), izp = izm;
+            if (var & 4) {
+              sx0 = xs_tab[2 * tx];
+              sx1 = xs_tab[2 * tx + 1];
+              ixa = xh_tab[2 * tx];
+              ixb = xh_tab[2 * tx + 1];
+              ixc = xh_tab[2 * tx + 2];
             }
-            a0 = stencil_general<float, CONJ>(G, c0, zc, om2 * m_prev.x, u0, l, u1, lo2(YM), lo2(YP), lo2(ZM),
-                                              lo2(ZP));
-            a1 = stencil_general<float, CONJ>(G, c1, zc, om2 * m_prev.y, u1, u0, r, hi2(YM), hi2(YP), hi2(ZM),
-                                              hi2(ZP));
+            if (var & 2) {
+              sy = ys_tab[ty];
+              iym = yh_tab[ty];
+              iyp = yh_tab[ty + 1];
+            }
+            if (var & 1) {
+              const C* zr = ztab + 3 * kp;
+              sz = __ldg(zr);
+              izm = __ldg(zr + 1);
+              izp = __ldg(zr + 2);
+            }
+            const float om0 = om2 * m_prev.x, om1 = om2 * m_prev.y;
+#define WRI_AX(AX_, AY_, AZ_)                                                                                 \
+  a0 = stencil_axes<AX_, AY_, AZ_>(ih2, om0, u0, l, u1, lo2(YM), lo2(YP), lo2(ZM), lo2(ZP), sx0, ixa, ixb, sy, iym, \
+                                iyp, sz, izm, izp);                                                           \
+  a1 = stencil_axes<AX_, AY_, AZ_>(ih2, om1, u1, u0, r, hi2(YM), hi2(YP), hi2(ZM), hi2(ZP), sx1, ixb, ixc, sy, iym, \
+                                iyp, sz, izm, izp);
+            switch (var) {
+              case 1: WRI_AX(false, false, true) break;
+              case 2: WRI_AX(false, true, false) break;
+              case 3: WRI_AX(false, true, true) break;
+              case 4: WRI_AX(true, false, false) break;
+              case 5: WRI_AX(true, false, true) break;
+              case 6: WRI_AX(true, true, false) break;
+              default: WRI_AX(true, true, true) break;
+            }
+#undef WRI_AX
           }
           if (own) {
             if (MODE == M_P1 && kp == src_k) {

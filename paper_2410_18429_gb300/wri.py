@@ -38,7 +38,8 @@ class WriSolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("dtype", C.c_int32),
                 ("warm_start", C.c_int32), ("max_refine", C.c_int32), ("refine_tol", C.c_double),
                 ("inner_tol", C.c_double), ("plain", C.c_int32), ("poll_every", C.c_int32),
-                ("tile", C.c_int32), ("zsplit", C.c_int32), ("kernel", C.c_int32)]
+                ("tile", C.c_int32), ("zsplit", C.c_int32), ("kernel", C.c_int32), ("order", C.c_int32),
+                ("l2_promotion", C.c_int32)]
 
 
 class WriError(RuntimeError):
@@ -169,10 +170,11 @@ def KERNEL_TMA(cfg: int = 0) -> int:
 
 
 def make_opts(tol=1e-6, max_iter=10000, dtype=C64, warm_start=False, max_refine=0, refine_tol=1e-10,
-              inner_tol=1e-3, plain=False, poll_every=0, tile=0, zsplit=0, kernel=KERNEL_AUTO) -> WriSolveOpts:
+              inner_tol=1e-3, plain=False, poll_every=0, tile=0, zsplit=0, kernel=KERNEL_AUTO,
+              order=0, l2_promotion=0) -> WriSolveOpts:
     return WriSolveOpts(float(tol), int(max_iter), int(dtype), int(bool(warm_start)), int(max_refine),
                         float(refine_tol), float(inner_tol), int(bool(plain)), int(poll_every), int(tile),
-                        int(zsplit), int(kernel))
+                        int(zsplit), int(kernel), int(order), int(l2_promotion))
 
 
 def workspace_size(groups: Sequence[GroupSpec], opts: WriSolveOpts) -> int:

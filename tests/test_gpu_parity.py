@@ -88,7 +88,7 @@ def test_fixed_iterations_match_oracle_cgls(W, dtype, tol, source_free):
         assert abs(rr.cpu().numpy()[s] - rr_k) <= max(tol, 1e-6) * rr_k * 10
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("source_free", [True, False])
 def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
     """TMA-pipelined phases (x extent a multiple of 4): ragged 32 x BY tiles, iterates of
