@@ -1,15 +1,20 @@
 """Benchmark of the batched SF-AWRI gradient (one JSON line on rank 0).
 
-Workload (N = 1): the frequency-dependent batch of 128 surface sources x 3
-frequencies (3 Hz on 64^3, 5 Hz on 96^3, 8 Hz on 128^3 physical nodes, each plus
-a 10-cell absorbing layer: 84^3, 116^3, 148^3 computational nodes), 96 borehole
-receivers, seeded layered + anomaly model, source-free mode, complex64 stencils with
-FP64 reductions.  One step = one gradient evaluation of all 384 systems: right-hand
-sides, ``--iters`` CGLS iterations per system (the fused, batched, graph-captured
-phases), the source-weight estimates and the gradient/objective accumulation.
+Workload (per GPU): the frequency-dependent batch of 128 surface sources x 3 frequencies
+(3 Hz on 64^3, 5 Hz on 96^3, 8 Hz on 128^3 physical nodes, each plus a 10-cell absorbing
+layer: 84^3, 116^3, 148^3 computational nodes), 96 borehole receivers, seeded layered +
+anomaly model, source-free mode, complex64 stencils with FP64 reductions.  One step = one
+gradient evaluation of all 384 systems: right-hand sides, ``--iters`` CGLS iterations per
+system (the fused, batched, graph-captured phases), the source-weight estimates and the
+gradient/objective accumulation.
 
-value = systems (source x frequency gradients) per second over all ranks.  The
-working set (~40 GB) is far larger than L2, so no flush is needed between steps.
+value = systems (source x frequency gradients) per second over all ranks.  With N ranks
+every rank evaluates its own shot record of 384 systems (weak scaling) and the gradients
+and objectives are summed over ranks (the method's one exchange step).  The working set
+(~40 GB per GPU) is far larger than L2, so no flush is needed between steps.
+
+``--impl reference`` times the CPU oracle (the repository has no other reference
+implementation) on a bounded sample of the same workload, on rank 0 only.
 """
 from __future__ import annotations
 
@@ -25,8 +30,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "WRI gradient src·freq/s at 128³ (GPt·iter/s, % HBM roofline) vs plain path"
-BYTES_PER_NODE_ITER = 80.0   # algorithmic bytes of one fused CGLS iteration per node and system (c64)
-MODEL_BYTES = 8.0            # m read by both phases (float32), shared by the systems of a group
+UNIT = "src·freq/s"
+BYTES_PER_NODE_SYS = 80.0  # one CGLS iteration, per node and system: phase 1 48 B + phase 2 32 B (c64)
+MODEL_BYTES = 8.0          # m (float32) read by both phases, per node of a group, shared by its systems
+K_POLL = 2                 # CG iterations per graph replay between host polls of the done-counter
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cg_iteration_traffic.json")
 
 
 def parse():
@@ -42,18 +50,30 @@ def parse():
                    help="keep only one frequency group (0: 3 Hz, 1: 5 Hz, 2: 8 Hz); profiling cases")
     p.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU legs")
     p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 z-march only, 2+c TMA configuration c")
-    p.add_argument("--order", type=int, default=0,
-                   help="TMA work order: 0 auto, 1 system-major, 2 tile-major, 3 z-chunk-major")
+    p.add_argument("--order", type=int, default=0, help="TMA work order (0 = library default)")
     p.add_argument("--zsplit", type=int, default=0, help="z-chunks per tile column (0 = library choice)")
     p.add_argument("--promo", type=int, default=0, help="TMA L2 promotion: 0 auto, 1 none, 2 64B, 3 128B, 4 256B")
+    p.add_argument("--cpu-iters", type=int, default=8, help="oracle CGLS iterations per CPU sample")
     return p.parse_args()
 
 
-def workload(nsrc, small):
+def workload(args, shard=0):
     import synth
-    if small:
-        return synth.workload_c4(nsrc=min(nsrc, 8), freqs=((3.0, 24), (5.0, 32), (8.0, 40)), nrec=24)
-    return synth.workload_c4(nsrc=nsrc)
+    if args.small:
+        groups = synth.workload_c4(nsrc=min(args.nsrc, 8), freqs=((3.0, 24), (5.0, 32), (8.0, 40)), nrec=24,
+                                   shard=shard)
+    else:
+        groups = synth.workload_c4(nsrc=args.nsrc, shard=shard)
+    if args.only_group >= 0:
+        groups = [groups[args.only_group]]
+    return groups
+
+
+def workload_name(args):
+    if args.small:
+        return "c4-batch-small"
+    base = "c4-batch: {} src x {{3 Hz 84^3, 5 Hz 116^3, 8 Hz 148^3}}".format(args.nsrc)
+    return base if args.only_group < 0 else base + f" (group {args.only_group} only)"
 
 
 def dist_env():
@@ -73,11 +93,11 @@ class Clocks:
     def __init__(self, dev):
         self.dev = dev
         self.p = None
-        self.out = None
+        self.path = f"/tmp/wri_clocks_{os.getpid()}.csv"
 
     def start(self):
         try:
-            self.out = open(os.devnull if False else "/tmp/wri_clocks.csv", "w")
+            self.out = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                        "-i", str(self.dev), "-lms", "200"], stdout=self.out,
                                       stderr=subprocess.DEVNULL)
@@ -92,7 +112,7 @@ class Clocks:
         self.out.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open("/tmp/wri_clocks.csv"):
+        for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
             if len(f) < 8:
                 continue
@@ -104,58 +124,82 @@ class Clocks:
             for nm, v in zip(names, f[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+        os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(grp, iters=25):
-    """Oracle CGLS (scipy.sparse, complex128) on one system: seconds per iteration."""
-    import numpy as np
-
+# ---------------------------------------------------------------- CPU oracle legs
+def _oracle_system(grp):
+    """(S, b) of the first system of a group, assembled by the oracle."""
     import oracle as O
     n = grp.spec.n
     A = O.helmholtz_matrix(grp.spec.shape, grp.spec.h, grp.omega, grp.m, grp.spec.npml, grp.v_max, grp.pml_R)
     rec = grp.rec_idx[grp.rec_off[0]:grp.rec_off[1]]
     S = O.augmented_operator(A, O.restriction(n, rec), grp.src[0], grp.lam, True)
     b = O.rhs(n, grp.src[0], grp.d[grp.rec_off[0]:grp.rec_off[1]], grp.lam)
+    return S, b
+
+
+def oracle_sample(S, b, iters):
+    """Seconds of ``iters`` oracle CGLS iterations (set-up of the first iteration excluded)."""
+    import oracle as O
     t0 = time.perf_counter()
-    O.cgls(S, b, tol=0.0, max_iter=2)
+    O.cgls(S, b, tol=0.0, max_iter=1)
     t1 = time.perf_counter()
-    O.cgls(S, b, tol=0.0, max_iter=2 + iters)
+    O.cgls(S, b, tol=0.0, max_iter=1 + iters)
     t2 = time.perf_counter()
-    return ((t2 - t1) - (t1 - t0)) / iters, (t2 - t0) + (t1 - t0)
+    return (t2 - t1) - (t1 - t0)
 
 
-def cpu_equivalent(groups, iters):
-    """CPU-oracle throughput for the bench step, from a bounded sample on the largest grid."""
+def cpu_rate(groups, step_iters, cpu_iters, samples, warm):
+    """Oracle throughput extrapolated to the bench step from bounded samples on the largest grid.
+
+    Returns (src·freq/s, node-iterations/s, seconds sampled, average busy threads)."""
+    import resource
     big = max(groups, key=lambda g: g.spec.n)
-    per_it, secs = cpu_oracle_rate(big)
-    rate = big.spec.n / per_it                       # node-iterations per second (one system)
-    node_iters = sum(g.nsys * g.spec.n for g in groups) * iters
-    step_s = node_iters / rate
+    S, b = _oracle_system(big)
+    for _ in range(warm):
+        oracle_sample(S, b, cpu_iters)
+    r0, w0 = resource.getrusage(resource.RUSAGE_SELF), time.perf_counter()
+    secs = sum(oracle_sample(S, b, cpu_iters) for _ in range(samples))
+    r1, w1 = resource.getrusage(resource.RUSAGE_SELF), time.perf_counter()
+    # threads the sample kept busy on average (scipy.sparse products run on one thread, numpy's
+    # BLAS dot products on several)
+    busy = ((r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)) / max(w1 - w0, 1e-9)
+    node_iter_rate = big.spec.n * cpu_iters * samples / secs
+    node_iters = sum(g.nsys * g.spec.n for g in groups) * step_iters
     nsys = sum(g.nsys for g in groups)
-    return {"value": nsys / step_s, "gpt_iter_s": rate / 1e9, "cores": 1, "kind": "oracle",
-            "sample": f"oracle CGLS (scipy.sparse complex128, serial) on 1 system of the "
-                      f"{big.spec.nx}^3 group, 25 iterations ({secs:.1f} s incl. warm-up); per-node rate "
-                      f"scaled to {nsys} systems x {iters} iterations", "unit": "src·freq/s"}
+    return nsys * node_iter_rate / node_iters, node_iter_rate, secs, busy
+
+
+def cpu_sample_text(groups, cpu_iters, samples):
+    big = max(groups, key=lambda g: g.spec.n)
+    return (f"oracle CGLS (scipy.sparse, complex128) on one system of the {big.spec.nx}^3 group: "
+            f"{samples} samples of {cpu_iters} iterations; the per-node-iteration rate is scaled to the step "
+            f"({sum(g.nsys for g in groups)} systems x the step's iterations)")
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    groups = workload(args.nsrc, args.small)
-    cb = cpu_equivalent(groups, args.iters)
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "src·freq/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "ms_per_step": 1e3 * sum(g.nsys for g in groups) / cb["value"],
-            "config": {"workload": "c4-batch", "iters_per_system": args.iters},
+    groups = workload(args)
+    nsys = sum(g.nsys for g in groups)
+    value, rate, secs, busy = cpu_rate(groups, args.iters, args.cpu_iters, args.steps, args.warmup)
+    cb = {"value": value, "unit": UNIT, "cores": max(1, round(busy)), "kind": "oracle",
+          "sample": cpu_sample_text(groups, args.cpu_iters, args.steps), "gpt_iter_s": rate / 1e9,
+          "seconds_sampled": secs, "busy_threads": busy, "host_threads": len(os.sched_getaffinity(0))}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "ms_per_step": 1e3 * nsys / value,
+            "config": {"workload": workload_name(args), "systems": nsys, "iters_per_system": args.iters,
+                       "l2": "working set >> L2 (no flush needed)"},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "src·freq/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -168,8 +212,8 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2410_18429_gb300 import wri
-    from paper_2410_18429_gb300.problem import to_device
     from paper_2410_18429_gb300.parallel_sum import allreduce_gradient
+    from paper_2410_18429_gb300.problem import to_device
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -177,22 +221,23 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    groups = workload(args.nsrc, args.small)
-    if args.only_group >= 0:
-        groups = [groups[args.only_group]]
+    groups = workload(args, shard=rank)
     specs = [to_device(g, wri.C64, dev) for g in groups]
     nsys = sum(g.nsys for g in groups)
-    n_nodes = [g.spec.n for g in groups]
-    K = 2
-    opts = wri.make_opts(tol=0.0, max_iter=args.iters, dtype=wri.C64, poll_every=K, kernel=args.kernel, order=args.order,
-                         zsplit=args.zsplit, l2_promotion=args.promo)
-    wsz = wri.workspace_size(specs, opts)
-    work = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    node_sys = sum(g.nsys * g.spec.n for g in groups)
+    opts = wri.make_opts(tol=0.0, max_iter=args.iters, dtype=wri.C64, poll_every=K_POLL, kernel=args.kernel,
+                         order=args.order, zsplit=args.zsplit, l2_promotion=args.promo)
+    work = torch.empty(wri.workspace_size(specs, opts), dtype=torch.uint8, device=dev)
     grads = [torch.zeros(g.spec.nz, g.spec.ny, g.spec.nx, dtype=torch.float64, device=dev) for g in groups]
     f = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
 
-    def step():
+    def step(solve_events=None):
+        if solve_events is not None:
+            solve_events[0].record(stream)
         it, rr, st = wri.solve(specs, opts, workspace=work)
+        if solve_events is not None:
+            solve_events[1].record(stream)
         a = wri.source_estimate(specs, wri.C64, workspace=work)
         for g in grads:
             g.zero_()
@@ -212,13 +257,14 @@ def main():
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    solve_ev = [(ev(), ev()) for _ in range(args.steps)]
+    e0, e1 = ev(), ev()
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
-        it = step()
+    for k in range(args.steps):
+        it = step(solve_ev[k])
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -231,25 +277,14 @@ def main():
         t = float(tt.item())
     iters_done = int(it.min().item())
     value = ws * nsys * args.steps / t
-    node_iters = sum(g.nsys * g.spec.n for g in groups) * iters_done
-    gpt = ws * node_iters * args.steps / t / 1e9
+    gpt = ws * node_sys * iters_done * args.steps / t / 1e9
 
-    # ---- roofline of the fused CG iteration (phase 1 + phase 2 kernels), live with CUDA events
-    def timed_solve(iters):
-        o = wri.make_opts(tol=0.0, max_iter=iters, dtype=wri.C64, poll_every=K, kernel=args.kernel, order=args.order,
-                         zsplit=args.zsplit, l2_promotion=args.promo)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        wri.solve(specs, o, workspace=work)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        return a0.elapsed_time(a1) / 1e3
-
-    timed_solve(10)
-    ta, tb = timed_solve(10), timed_solve(70)
-    t_iter = (tb - ta) / 60.0
-    alg_bytes = sum(g.nsys * g.spec.n * BYTES_PER_NODE_ITER + g.spec.n * MODEL_BYTES for g in groups)
+    # ---- roofline of one fused CG iteration (phase 1 + phase 2), from the solves of the timed steps:
+    # each solve is its set-up (one stencil) plus iters_done iterations, timed with CUDA events on the
+    # stream the graph replays are launched on
+    t_solve = statistics.mean(a.elapsed_time(b) for a, b in solve_ev) / 1e3
+    t_iter = t_solve / iters_done
+    alg_bytes = node_sys * BYTES_PER_NODE_SYS + sum(g.spec.n for g in groups) * MODEL_BYTES
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -259,14 +294,15 @@ def main():
     achieved = alg_bytes / t_iter / 1e9
     traffic = None
     try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "cg_iteration_traffic.json")))
+        prof = json.load(open(TRAFFIC_FILE))
         if prof.get("kernel_version") == wri.version():
-            traffic = prof.get("bytes_per_iteration")
-    except OSError:
+            traffic = prof["bytes_per_node_system"] * node_sys
+    except (OSError, KeyError, ValueError):
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_march phase1+phase2 (one fused CGLS iteration, all systems)",
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+                "traffic": traffic, "algorithmic_bytes": alg_bytes,
+                "kernel": "k_phase_tma2 phase 1 + phase 2 (one fused CGLS iteration over all systems)",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -290,8 +326,8 @@ def main():
         timed_plain(5)
         pa, pb = timed_plain(10), timed_plain(60)
         plain_per_sys_iter = (pb - pa) / 50.0
-        fused_per_sys_iter_big = t_iter * (g0.spec.n / sum(g.nsys * g.spec.n for g in groups))
-        plain_step = sum(g.nsys * g.spec.n for g in groups) * iters_done * plain_per_sys_iter / g0.spec.n
+        fused_per_sys_iter_big = t_iter * (g0.spec.n / node_sys)
+        plain_step = node_sys * iters_done * plain_per_sys_iter / g0.spec.n
         extras["plain"] = {"per_system_iter_ms_148": plain_per_sys_iter * 1e3,
                            "fused_per_system_iter_ms_148": fused_per_sys_iter_big * 1e3,
                            "speedup_per_iteration": plain_per_sys_iter / fused_per_sys_iter_big,
@@ -325,7 +361,7 @@ def main():
 
         e2e_step()
         torch.cuda.synchronize()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0, c1 = ev(), ev()
         ne = max(2, args.steps // 2)
         c0.record(stream)
         for _ in range(ne):
@@ -333,26 +369,33 @@ def main():
         c1.record(stream)
         torch.cuda.synchronize()
         te = c0.elapsed_time(c1) / 1e3
-        extras["e2e"] = {"value": nsys * ne / te, "unit": "src·freq/s", "h2d_bytes_per_step": h2d,
+        extras["e2e"] = {"value": nsys * ne / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h}
         if ws == 1:
-            extras["cpu_baseline"] = cpu_equivalent(groups, iters_done)
+            samples = 4
+            val, rate, secs, busy = cpu_rate(groups, iters_done, args.cpu_iters * 2, samples, 1)
+            extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": max(1, round(busy)), "kind": "oracle",
+                                      "sample": cpu_sample_text(groups, args.cpu_iters * 2, samples),
+                                      "gpt_iter_s": rate / 1e9, "seconds_sampled": secs, "busy_threads": busy,
+                                      "host_threads": len(os.sched_getaffinity(0))}
 
-    # kernel launches per step: setup + init + export, 2 per CG iteration (graph batches of K), estimate,
-    # gradient + data term
-    graph_launches = -(-(iters_done + 1) // K)
-    launches = 3 + 2 * K * graph_launches + 1 + 2
+    # kernels of libwri per step: set-up of the right-hand sides, z tables, initial S^H b, 2 phase kernels
+    # per CG iteration in graph replays of K_POLL iterations (the last replay holds the x-only pass),
+    # result export, source estimate, gradient and data term
+    replays = -(-(iters_done + 1) // K_POLL)
+    launches = 3 + 2 * K_POLL * replays + 1 + 1 + 2
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "src·freq/s", "n_gpus": ws, "steps": args.steps,
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp64 reductions)", "data": "synthetic",
-                "config": {"workload": "c4-batch: 128 src x {3 Hz 84^3, 5 Hz 116^3, 8 Hz 148^3}"
-                                       if not args.small else "c4-batch-small",
-                           "systems": nsys, "iters_per_system": iters_done, "tol": 0.0,
-                           "nodes": n_nodes, "parallelism": f"replicas x{ws} (sources sharded, gradient all-reduce)",
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+                "config": {"workload": workload_name(args), "systems_per_gpu": nsys,
+                           "iters_per_system": iters_done, "tol": 0.0,
+                           "nodes": [g.spec.n for g in groups],
+                           "parallelism": f"data parallel x{ws}: one shot record per GPU, gradient all-reduce",
+                           "precision": "complex64 vectors and stencils, FP64 reductions and scalars",
                            "l2": "working set >> L2 (no flush needed)"},
                 "gpt_iter_s": gpt, "t_cg_iter_ms": t_iter * 1e3, "roofline": roofline, "clocks": clk,
-                "gpu_launches": launches * args.steps}
+                "gpu_launches": launches * args.steps, "library": wri.version()}
         line.update(extras)
         if "e2e" not in line:
             line["e2e"] = None

@@ -5,6 +5,7 @@ links the shared library.  Usage: ``python -m paper_2410_18429_gb300.build``.
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import shutil
 import subprocess
@@ -36,15 +37,29 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def source_hash() -> str:
+    """Hash of every kernel and interface source; libwri reports it in wri_version() so that
+    profiles taken on one build are recognised as stale on another."""
+    h = hashlib.sha256()
+    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h", ".inc")))
+    for f in files + ["../../include/wri.h"]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:12]
+
+
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    digest = source_hash()
+    stamp = os.path.join(BUILD, "source_hash.txt")
+    old = open(stamp).read().strip() if os.path.exists(stamp) else ""
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
         obj = os.path.join(BUILD, s.replace(".cu", ".o"))
-        if force or _stale(obj, src):
-            jobs.append([cc, *FLAGS, *ARCH, "-c", src, "-o", obj])
+        if force or _stale(obj, src) or (s == "wri_api.cu" and old != digest):
+            jobs.append([cc, *FLAGS, *ARCH, f'-DWRI_SRC_HASH="{digest}"', "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,6 +75,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         tmp = LIB + ".tmp"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(digest + "\n")
     return LIB
 
 

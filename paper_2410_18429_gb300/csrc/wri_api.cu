@@ -148,10 +148,11 @@ struct Plan {
   long long nitems = 0;
   long long nparts = 0;
   size_t off_sys = 0, off_rec = 0, off_part = 0, off_rem = 0, off_lamd = 0, off_r2 = 0;
+  size_t off_r2_64 = 0, off_r2_in = 0;  // refinement: FP64 receiver residual master, complex64 inner r2
   size_t aux_total = 0, total = 0;
   GroupDev g[WRI_MAXG];
   size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][2], v_s[WRI_MAXG], v_t1[WRI_MAXG];
-  size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG];
+  size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG], v_q64[WRI_MAXG], v_g32[WRI_MAXG];
   size_t off_ztab[WRI_MAXG];
   std::vector<int> rec_base;  // first receiver entry of every group
 };
@@ -224,6 +225,13 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
   off += align_up((size_t)P.rlbytes * std::max(P.nnz_total, 1));
   P.off_r2 = off;
   off += align_up((size_t)P.rlbytes * std::max(P.nnz_total, 1));
+  P.off_r2_64 = P.off_r2_in = 0;
+  if (P.ir) {
+    P.off_r2_64 = off;
+    off += align_up(16 * (size_t)std::max(P.nnz_total, 1));
+    P.off_r2_in = off;
+    off += align_up(8 * (size_t)std::max(P.nnz_total, 1));
+  }
   for (int gi = 0; gi < ngroups; ++gi) {
     P.off_ztab[gi] = off;
     off += align_up(sizeof(float) * 2 * 2 * 3 * (size_t)groups[gi].grid.nz);
@@ -236,12 +244,14 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
     P.v_p[gi][1] = off; off += vb;
     P.v_s[gi] = off; off += vb;
     P.v_t1[gi] = off; off += vb;
-    P.v_x32[gi] = P.v_x64[gi] = P.v_r64[gi] = 0;
+    P.v_x32[gi] = P.v_x64[gi] = P.v_r64[gi] = P.v_q64[gi] = P.v_g32[gi] = 0;
     if (P.ir) {
       const size_t nn = (size_t)P.g[gi].nsys * (size_t)P.g[gi].n;
       P.v_x32[gi] = off; off += align_up(8 * nn);
       P.v_x64[gi] = off; off += align_up(16 * nn);
       P.v_r64[gi] = off; off += align_up(16 * nn);
+      P.v_q64[gi] = off; off += align_up(16 * nn);
+      P.v_g32[gi] = off; off += align_up(8 * nn);
     }
   }
   P.total = off;
@@ -337,6 +347,11 @@ Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_
   b.r2 = ws + P.off_r2;
   b.lamd = ws + P.off_lamd;
   b.remaining = (int*)(ws + P.off_rem);
+  if (P.ir) {
+    b.r2_64 = ws + P.off_r2_64;
+    b.r2_in = ws + P.off_r2_in;
+    if (inner_view) b.r2 = b.r2_in;  // the FP32 inner solve keeps its receiver residual in complex64
+  }
   for (int gi = 0; gi < P.ngroups; ++gi) {
     GroupDev G = P.g[gi];
     const wri_group& U = groups[gi];
@@ -355,6 +370,8 @@ Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_
     G.x = (P.ir && inner_view) ? (void*)(ws + P.v_x32[gi]) : U.u;
     G.x64 = P.ir ? ws + P.v_x64[gi] : nullptr;
     G.r64 = P.ir ? ws + P.v_r64[gi] : nullptr;
+    G.q64 = P.ir ? ws + P.v_q64[gi] : nullptr;
+    G.gvec = (P.ir && inner_view) ? ws + P.v_g32[gi] : nullptr;
     G.ztab = (const float2*)(ws + P.off_ztab[gi]);
     b.g[gi] = G;
   }
@@ -549,14 +566,21 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
 }
 
 // ---------------------------------------------------------------- FP64 iterative refinement
+// Augmented-system refinement (Bjorck) of min ||S x - b|| with complex64 inner solves: the
+// solution x64 and the residual r64 live in FP64.  Each outer step computes, with FP64
+// stencils, q = b - S x64, the outer test c = S^H q (||c|| / ||S^H b|| <= refine_tol), the
+// forcing f = q - r64 and g' = S^H r64; the complex64 CGLS inner solve (phase 2 adds g')
+// then returns dx and dr = f - S dx, and x64 += dx, r64 += dr.  The inner accuracy needed
+// scales with u32 kappa(S), not with u32 kappa(S)^2 as for refinement on the normal equations.
 int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o, const Plan& P, char* ws,
                   cudaStream_t st) {
   DevCtx* c = ctx();
   if (!c) return WRI_ECUDA;
-  Batch outer = solver_batch(groups, P, ws, false);  // FP64 views: x = x64, r1[0] = r64
+  // FP64 views: the residual kernel reads x64 and writes q64 (nodes) and b.r2 = q2 (receivers)
+  Batch outer = solver_batch(groups, P, ws, false);
   for (int gi = 0; gi < P.ngroups; ++gi) {
     outer.g[gi].x = outer.g[gi].x64;
-    outer.g[gi].r1[0] = outer.g[gi].r64;
+    outer.g[gi].r1[0] = outer.g[gi].q64;
   }
   outer.max_iter = o->max_iter;
   outer.tol = o->tol;
@@ -564,20 +588,26 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
   outer.inner_tol = o->inner_tol;
   outer.max_refine = o->max_refine;
   outer.warm = o->warm_start ? 1 : 0;
-  Batch inner = solver_batch(groups, P, ws, true);  // FP32 views: x = x32
+  // complex64 views: x = dx, r2 = r2_in, gvec = g'
+  Batch inner = solver_batch(groups, P, ws, true);
   inner.max_iter = o->max_iter;
-  inner.cgnr = 1;
-  // lambda d in FP64, x64 = warm ? u : 0, x32 = 0
+  void* u[WRI_MAXG] = {};
+  for (int gi = 0; gi < P.ngroups; ++gi) u[gi] = groups[gi].u;
+  // lambda d in FP64 (lamd and q2), x64 = warm ? u : 0, r64 = 0, dx = 0
   WRI_CK(launch_setup_rhs(4, 8, outer, P.nsys_total, st));
-  {
-    Batch z = inner;
-    for (int gi = 0; gi < P.ngroups; ++gi) z.g[gi].d = groups[gi].u;
-    WRI_CK(launch_ir_init(z, o->warm_start ? 1 : 0, st));
-  }
-  if (o->warm_start) {  // ||S^H b|| with the FP64 stencil
+  WRI_CK(launch_ir_init(inner, u, o->warm_start ? 1 : 0, st));
+  if (o->warm_start) {  // ||S^H b|| with the FP64 stencil (q2 still holds lambda d)
     Batch r = outer;
     r.flavor = SH_REF;
     WRI_CK(launch_march_f64_to_f32(M_SH, P.by, r, 0, st));
+  }
+  // g' = S^H r64 (FP64 stencil on r64 and r2_64, rounded into the inner gvec)
+  Batch gb = outer;
+  gb.flavor = SH_PLAIN;
+  gb.r2 = gb.r2_64;
+  for (int gi = 0; gi < P.ngroups; ++gi) {
+    gb.g[gi].r1[0] = gb.g[gi].r64;
+    gb.g[gi].s = const_cast<void*>(inner.g[gi].gvec);
   }
   const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
   for (int outer_k = 0;; ++outer_k) {
@@ -585,21 +615,19 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
     Batch r = outer;
     r.outer = outer_k;
     r.flavor = SH_REFINE;
-    WRI_CK(march(8, 8, M_RES, false, P.by, r, st));
-    WRI_CK(launch_march_f64_to_f32(M_SH, P.by, r, 0, st));
+    WRI_CK(march(8, 8, M_RES, false, P.by, r, st));                // q = b - S x64
+    WRI_CK(launch_ir_forcing(inner, outer.r2, st));                // f = q - r64 (complex64)
+    WRI_CK(launch_march_f64_to_f32(M_SH, P.by, r, 0, st));         // c = S^H q, outer test
     WRI_CK(cudaMemcpyAsync(c->pinned, outer.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
     WRI_CK(cudaStreamSynchronize(st));
     if (*c->pinned <= 0) break;
-    const int rc = run_loop(P, inner, inner, M_P2N, std::min(K, o->max_iter + 1), o->max_iter, st);
+    WRI_CK(launch_march_f64_to_f32(M_SH, P.by, gb, 0, st));        // g' = S^H r64
+    const int rc = run_loop(P, inner, inner, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st);
     if (rc != WRI_OK) return rc;
-    Batch a = inner;
-    for (int gi = 0; gi < P.ngroups; ++gi) a.g[gi].x64 = outer.g[gi].x64;
-    WRI_CK(launch_ir_accum(a, 0, st));
+    WRI_CK(launch_ir_update(inner, st));                           // x64 += dx, r64 += dr
     if (outer_k > o->max_refine + 1) return WRI_ECUDA;
   }
-  Batch f = inner;
-  for (int gi = 0; gi < P.ngroups; ++gi) f.g[gi].t1 = groups[gi].u;
-  WRI_CK(launch_ir_accum(f, 1, st));
+  WRI_CK(launch_ir_final(inner, u, st));
   return WRI_OK;
 }
 
@@ -967,6 +995,9 @@ const char* wri_strerror(int code) {
   return "unknown error code";
 }
 
-const char* wri_version(void) { return "libwri 0.1 (sm_103a)"; }
+#ifndef WRI_SRC_HASH
+#define WRI_SRC_HASH "unknown"
+#endif
+const char* wri_version(void) { return "libwri 0.2 (sm_103a) src " WRI_SRC_HASH; }
 
 }  // extern "C"

@@ -88,7 +88,6 @@ enum Mode : int {
   M_RES = 2,    // r1 = b1 - Z A x, r2 = lambda (d - P x)
   M_P1 = 3,     // p = s + beta p_old, t1 = Z A p, x += alpha_prev p_old
   M_P2 = 4,     // r1 = r1_old - alpha t1, s = A^H r1 (CGLS)
-  M_P2N = 5,    // s = s - alpha A^H t1 (CG on the normal equations, refinement inner solve)
   M_GRAD = 6,   // g += omega^2 Re(conj(w u)(A u - a e)), f += 1/2 |A u - a e|^2
 };
 
@@ -97,7 +96,8 @@ enum ShFlavor : int {
   SH_INIT = 0,      // cold start: F = b1 (point), writes r1 = b1, x = 0; sets snorm_b
   SH_REF = 1,       // F = b1 (point), computes ||S^H b|| only (warm start); writes r1 = b1
   SH_WARM = 2,      // F = r1 (from M_RES), starts the solve from the stored x
-  SH_REFINE = 3,    // F = r64 (FP64 residual), output cast to the inner s; outer test
+  SH_REFINE = 3,    // F = q64 = b - S x64 (FP64), output c = S^H q cast to the inner s; outer test
+  SH_PLAIN = 4,     // F = r64 (FP64 residual iterate), output S^H r64 cast to gvec; no scalars
 };
 
 // ------------------------------------------------------------------ batch descriptors
@@ -145,8 +145,10 @@ struct GroupDev {
   void* p[2];               // [nsys][n] search direction, ping-pong
   void* s;                  // [nsys][n] normal-equation residual S^H r
   void* t1;                 // [nsys][n] Z A p
-  void* x64;                // [nsys][n] double2 refinement master (or null)
-  void* r64;                // [nsys][n] double2 FP64 residual (or null)
+  void* x64;                // [nsys][n] double2 refinement master of the solution (or null)
+  void* r64;                // [nsys][n] double2 refinement master of the residual b1 - Z A x (or null)
+  void* q64;                // [nsys][n] double2 true residual b1 - Z A x64 of the outer step (or null)
+  const void* gvec;         // [nsys][n] complex64 S^H r64, added to s in phase 2 (or null)
   double* grad;             // [n] gradient accumulator (gradient kernel only)
   const float2* ztab;       // [2][nz][3] z-axis coefficients (s_z, 1/(s_z(k-1/2) h^2), 1/(s_z(k+1/2) h^2)),
                             // [0] for A, [1] conjugated for A^H; FP32, built once per solve
@@ -160,12 +162,13 @@ struct Batch {
   double* partial;      // per (system, tile) FP64 partial sums
   const int* rec_idx;   // batch-wide receiver nodes
   void* r2;             // batch-wide receiver residual (type of the kernel's stencil)
+  void* r2_64;          // refinement: FP64 receiver part of the residual master (or null)
+  void* r2_in;          // refinement: complex64 receiver residual of the inner solve (or null)
   const void* lamd;     // batch-wide lambda*d (same type as r2)
   int* remaining;       // systems not yet DONE
   double* f;            // objective accumulator (gradient kernel only)
   int max_iter;
   int flavor;           // kernel-specific sub-mode
-  int cgnr;             // 1: inner solve on the normal equations (no data-space residual)
   int order;            // TMA phases: work-item order, 0 = systems fastest, 1 = tiles of a system
                         // consecutive, 2 = z-chunk slowest (the resident wave shares z-slabs),
                         // 3 = blocks of sblock systems, tiles in order, systems fastest in a block

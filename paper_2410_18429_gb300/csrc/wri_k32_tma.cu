@@ -58,12 +58,42 @@ static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStr
   return cudaGetLastError();
 }
 
-int tma_config_count() { return 9; }
+template <int MODE, int BY, int S, int MINB>
+static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
+  static int occ = -1;
+  const size_t smem = WsLayout<MODE, BY>::bytes(S);
+  auto kern = k_phase_ws<MODE, BY, S, MINB>;
+  constexpr int threads = 16 * BY + 32;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    occ = n > 0 ? n : 1;
+  }
+  if (grid <= 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long g = (long long)sms * occ;
+    grid = (int)(g < b.nitems ? g : b.nitems);
+    if (grid < 1) grid = 1;
+  }
+  kern<<<grid, threads, smem, st>>>(b, T);
+  return cudaGetLastError();
+}
+
+int tma_config_count() { return 14; }
 
 // config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4) with one node per thread;
 // 4 -> (16, 4), 5 -> (16, 3), 6 -> (8, 6), 7 -> (8, 3; 5 CTAs/SM), 8 -> (8, 4; 4 CTAs/SM) with two
-// x-adjacent nodes per thread
-int tma_config_by(int cfg) { return (cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5) ? 16 : 8; }
+// x-adjacent nodes per thread; warp-specialised (copy warp + consumer warps, two nodes per
+// thread): 9 -> (8, 4 stages; 4 CTAs/SM), 10 -> (8, 4; 5 CTAs/SM), 11 -> (8, 6; 3), 12 -> (16, 4; 2),
+// 13 -> (8, 5; 4)
+int tma_config_by(int cfg) { return (cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5 || cfg == 12) ? 16 : 8; }
 
 cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   if (b.nitems <= 0) return cudaSuccess;
@@ -91,6 +121,19 @@ cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T,
   WRI_TMA2_CASE(M_P1, 8, 8, 4, 4)
   WRI_TMA2_CASE(M_P2, 8, 8, 4, 4)
 #undef WRI_TMA2_CASE
+#define WRI_WS_CASE(M, C_, BY_, S_, MB_) \
+  if (mode == M && cfg == C_) return launch_ws<M, BY_, S_, MB_>(b, T, grid, st);
+  WRI_WS_CASE(M_P1, 9, 8, 4, 4)
+  WRI_WS_CASE(M_P2, 9, 8, 4, 4)
+  WRI_WS_CASE(M_P1, 10, 8, 4, 5)
+  WRI_WS_CASE(M_P2, 10, 8, 4, 5)
+  WRI_WS_CASE(M_P1, 11, 8, 6, 3)
+  WRI_WS_CASE(M_P2, 11, 8, 6, 3)
+  WRI_WS_CASE(M_P1, 12, 16, 4, 2)
+  WRI_WS_CASE(M_P2, 12, 16, 4, 2)
+  WRI_WS_CASE(M_P1, 13, 8, 5, 4)
+  WRI_WS_CASE(M_P2, 13, 8, 5, 4)
+#undef WRI_WS_CASE
   return cudaErrorInvalidValue;
 }
 

@@ -19,8 +19,11 @@ cudaError_t launch_setup_rhs(int dtype_bytes, int rl_bytes, const Batch& b, int 
 cudaError_t launch_ztable(const Batch& b, cudaStream_t st);
 cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* relres, int32_t* status,
                           cudaStream_t st);
-cudaError_t launch_ir_init(const Batch& b, int warm, cudaStream_t st);
-cudaError_t launch_ir_accum(const Batch& b, int final_cast, cudaStream_t st);
+// FP64 refinement (b: inner complex64 view; u: the caller's wavefields, one per group)
+cudaError_t launch_ir_init(const Batch& b, void* const* u, int warm, cudaStream_t st);
+cudaError_t launch_ir_forcing(const Batch& b, const void* q2, cudaStream_t st);
+cudaError_t launch_ir_update(const Batch& b, cudaStream_t st);
+cudaError_t launch_ir_final(const Batch& b, void* const* u, cudaStream_t st);
 cudaError_t launch_source_estimate(int rbytes, const Batch& b, int nsys_total, double* alpha_out, cudaStream_t st);
 cudaError_t launch_data_term(int rbytes, const Batch& b, int nsys_total, cudaStream_t st);
 

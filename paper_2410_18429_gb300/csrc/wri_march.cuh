@@ -32,16 +32,28 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum (fixed order); every thread must call it.  Result valid in thread 0.
-template <int NT>
+// Barrier of the threads that take part in a reduction: the whole CTA ...
+struct CtaSync {
+  static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+// ... or only the first NC threads (named barrier 1), when other warps of the CTA run
+// independently (the copy-issuing warp of the warp-specialised phases).
+template <int NC>
+struct FirstThreadsSync {
+  static __device__ __forceinline__ void sync() { asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory"); }
+};
+
+// Deterministic block sum (fixed order) over the NT threads of SYNC; every one of them must
+// call it.  Result valid in thread 0.
+template <int NT, typename SYNC = CtaSync>
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);
   const int ltid = threadIdx.y * blockDim.x + threadIdx.x;  // any block shape
   const int lane = ltid & 31;
   const int wid = ltid >> 5;
-  __syncthreads();
+  SYNC::sync();
   if (lane == 0) red[wid] = v;
-  __syncthreads();
+  SYNC::sync();
   double r = 0.0;
   if (wid == 0) {
     r = (lane < NT / 32) ? red[lane] : 0.0;
@@ -148,6 +160,26 @@ __device__ __forceinline__ cx<R> stencil_interior(R ih2, R om2m, cx<R> u, cx<R> 
                                                   cx<R> uyp, cx<R> uzm, cx<R> uzp) {
   const cx<R> sum = (uxm + uxp) + (uym + uyp) + (uzm + uzp);
   return mkc(om2m * u.x + ih2 * (sum.x - R(6) * u.x), om2m * u.y + ih2 * (sum.y - R(6) * u.y));
+}
+
+// (A F)[node] (CONJ = false) or (A^H F)[node] (CONJ = true) at one node of a system's field F,
+// with the general coefficients (7 loads, Dirichlet outside the grid).
+template <typename R, bool CONJ>
+__device__ cx<R> stencil_at(const GroupDev& G, const cx<R>* F, long long node) {
+  const long long plane = (long long)G.nx * G.ny;
+  const int k = (int)(node / plane);
+  const long long rem = node - (long long)k * plane;
+  const int j = (int)(rem / G.nx);
+  const int i = (int)(rem - (long long)j * G.nx);
+  auto at = [&](int ii, int jj, int kk) -> cx<R> {
+    if (ii < 0 || jj < 0 || kk < 0 || ii >= G.nx || jj >= G.ny || kk >= G.nz) return czero<R>();
+    return F[(long long)kk * plane + (long long)jj * G.nx + ii];
+  };
+  const XYCoef<R> c = xy_coef<R, CONJ>(G, i, j);
+  const ZCoef<R> z = z_coef<R, CONJ>(G, k);
+  const R om2m = pick<R>(G.omega * G.omega, G.om2f) * model_at<R>(G.m, G.m_double, node);
+  return stencil_general<R, CONJ>(G, c, z, om2m, at(i, j, k), at(i - 1, j, k), at(i + 1, j, k), at(i, j - 1, k),
+                                  at(i, j + 1, k), at(i, j, k - 1), at(i, j, k + 1));
 }
 
 }  // namespace wri

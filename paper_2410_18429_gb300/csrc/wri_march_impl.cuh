@@ -16,8 +16,9 @@ __device__ __forceinline__ cx<R> ldg_c(const cx<R>* p) {
 
 // ------------------------------------------------------------------ finalizers
 // Run by every thread of the CTA that completed the last tile of system `sd`.
-// NT is the number of threads of the CTA (any 2-D shape).
-template <typename R, typename OR, int MODE, int NT>
+// NT is the number of threads that run it (the whole CTA, any 2-D shape, or the first NT
+// threads of a 1-D CTA with SYNC = FirstThreadsSync<NT>).
+template <typename R, typename OR, int MODE, int NT, typename SYNC = CtaSync>
 __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, bool xonly, double* red,
                          double* bcast) {
   typedef cx<R> C;
@@ -42,7 +43,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     const double* pp = b.partial + sd->part_off;
     for (int t = tid; t < G.ntiles; t += NT) part += __ldcg(pp + t);
   }
-  part = block_sum<NT>(part, red);
+  part = block_sum<NT, SYNC>(part, red);
 
   // receiver terms
   const int rb = sd->rec_begin, re = sd->rec_end;
@@ -54,6 +55,15 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     if (MODE == M_P1) {
       const C pn = ldcg_c((const C*)G.p[cur ^ 1] + node);
       rec += (double)lam * (double)lam * (double)abs2(pn);
+    } else if (MODE == M_SH && sizeof(R) != sizeof(OR) && b.flavor != SH_INIT && b.flavor != SH_REF) {
+      // FP64 stencil rounded to complex64 (the refinement's S^H q and S^H r64): near convergence
+      // A^H F and lambda P^T r2 nearly cancel at a receiver, so they are added in FP64 (the node
+      // value recomputed) before the single rounding
+      OC* S = (OC*)G.s;
+      const C af = stencil_at<R, true>(G, (const C*)G.r1[0] + off, b.rec_idx[k]);
+      const C sn = af + lam * r2[k];
+      S[node] = to_c(sn, OR(0));
+      rec += (double)abs2(sn) - (double)abs2(af);
     } else if (MODE == M_SH || MODE == M_P2) {
       OC* S = (OC*)G.s;
       const OC sv = ldcg_c(S + node);
@@ -66,21 +76,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
       r2[k] = ((const C*)b.lamd)[k] - lam * xv;
     }
   }
-  if (MODE == M_P2N) {
-    // s -= alpha lambda^2 P^T P p: p of this iteration sits in p[(iter + 1) & 1] (iter advances below)
-    const double a = sd->alpha;
-    OC* S = (OC*)G.s;
-    for (int k = rb + tid; k < re; k += NT) {
-      const long long node = off + b.rec_idx[k];
-      const OC sv = ldcg_c(S + node);
-      const C pn = ldcg_c((const C*)G.p[cur ^ 1] + node);
-      const C sn_r = to_c(sv, R(0)) - R(a * (double)lam * (double)lam) * pn;
-      const OC sn = to_c(sn_r, OR(0));
-      S[node] = sn;
-      rec += (double)abs2(sn) - (double)abs2(sv);
-    }
-  }
-  rec = block_sum<NT>(rec, red);
+  rec = block_sum<NT, SYNC>(rec, red);
 
   if (tid == 0) {
     const double tot = part + rec;
@@ -97,7 +93,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
       sd->delta = delta;
       sd->alpha = alpha;
       *bcast = alpha;
-    } else if (MODE == M_P2 || MODE == M_P2N) {
+    } else if (MODE == M_P2) {
       const double g = tot;
       const int it = sd->iter + 1;
       sd->iter = it;
@@ -120,7 +116,9 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     } else if (MODE == M_SH) {
       const double g = tot;
       const double rn = sqrt(g);
-      if (b.flavor == SH_REF) {
+      if (b.flavor == SH_PLAIN) {
+        // S^H r64 of the refinement: output vector only, no scalar changes
+      } else if (b.flavor == SH_REF) {
         sd->snorm_b = rn;
       } else if (b.flavor == SH_INIT || b.flavor == SH_WARM) {
         if (b.flavor == SH_INIT) sd->snorm_b = rn;
@@ -178,8 +176,8 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     }
     sd->ticket = 0u;
   }
-  if (MODE == M_P1 && !b.cgnr) {
-    __syncthreads();
+  if (MODE == M_P1) {
+    SYNC::sync();
     const double a = *bcast;
     if (a != 0.0) {
       for (int k = rb + tid; k < re; k += NT) {
@@ -224,11 +222,12 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
 
     // ---- what this item does (uniform across the CTA)
     int state = ST_ACTIVE;
-    if (MODE == M_P1 || MODE == M_P2 || MODE == M_P2N) state = sd->state;
+    if (MODE == M_P1 || MODE == M_P2) state = sd->state;
     bool skip = false;
     if (MODE == M_P1) skip = (state == ST_DONE);
-    if (MODE == M_P2 || MODE == M_P2N) skip = (state != ST_ACTIVE);
-    if ((MODE == M_SH || MODE == M_RES) && b.flavor == SH_REFINE) skip = sd->outer_done != 0;
+    if (MODE == M_P2) skip = (state != ST_ACTIVE);
+    if ((MODE == M_SH || MODE == M_RES) && (b.flavor == SH_REFINE || b.flavor == SH_PLAIN))
+      skip = sd->outer_done != 0;
     if (skip) continue;
     const bool xonly = (MODE == M_P1 && state == ST_FINISHING);
 
@@ -308,13 +307,10 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
           Fb = (const C*)G.t1 + off;
           coef = -R(sd->alpha);
           Fst = (C*)G.r1[cur ^ 1] + off;
-        } else if (MODE == M_P2N) {
-          Fa = (const C*)G.t1 + off;
         }
         C a_src = czero<R>();
         if (MODE == M_RES && !G.masked) a_src = mkc(R(G.alpha[2 * sl]), R(G.alpha[2 * sl + 1]));
         if (MODE == M_GRAD) a_src = mkc(R(G.alpha[2 * sl]), R(G.alpha[2 * sl + 1]));
-        const R step = (MODE == M_P2N) ? R(sd->alpha) : R(0);
 
         // F at any node (no side effects)
         auto fieldF = [&](long long node) -> C {
@@ -411,15 +407,12 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
               if (sizeof(R) == 4) accf += (float)abs2(t);
               else accd += (double)abs2(t);
             } else if (MODE == M_P2) {
+              // refinement inner solve: s = S^H r + S^H r64, the normal residual of the correction
+              // system S^H S dx = S^H f - g with g = -S^H r64
+              if (G.gvec) AF = AF + to_c(((const float2*)G.gvec)[gnode], R(0));
               ((C*)G.s)[gnode] = AF;
               if (sizeof(R) == 4) accf += (float)abs2(AF);
               else accd += (double)abs2(AF);
-            } else if (MODE == M_P2N) {
-              C* S = (C*)G.s;
-              const C sn = S[gnode] - step * AF;
-              S[gnode] = sn;
-              if (sizeof(R) == 4) accf += (float)abs2(sn);
-              else accd += (double)abs2(sn);
             } else if (MODE == M_GRAD) {
               C r = AF;
               if (node == src) r = r - a_src;

@@ -32,13 +32,29 @@ cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* r
   return cudaGetLastError();
 }
 
-cudaError_t launch_ir_init(const Batch& b, int warm, cudaStream_t st) {
-  k_ir_init<<<2048, 256, 0, st>>>(b, warm);
+static IrU ir_u(void* const* u, int ngroups) {
+  IrU U;
+  for (int g = 0; g < WRI_MAXG; ++g) U.u[g] = g < ngroups ? (float2*)u[g] : nullptr;
+  return U;
+}
+
+cudaError_t launch_ir_init(const Batch& b, void* const* u, int warm, cudaStream_t st) {
+  k_ir_init<<<1024, 256, 0, st>>>(b, ir_u(u, b.ngroups), warm);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ir_accum(const Batch& b, int final_cast, cudaStream_t st) {
-  k_ir_accum<<<2048, 256, 0, st>>>(b, final_cast);
+cudaError_t launch_ir_forcing(const Batch& b, const void* q2, cudaStream_t st) {
+  k_ir_forcing<<<1024, 256, 0, st>>>(b, (const double2*)q2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir_update(const Batch& b, cudaStream_t st) {
+  k_ir_update<<<1024, 256, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir_final(const Batch& b, void* const* u, cudaStream_t st) {
+  k_ir_final<<<1024, 256, 0, st>>>(b, ir_u(u, b.ngroups));
   return cudaGetLastError();
 }
 

@@ -54,66 +54,122 @@ __global__ void k_export(const SysDev* sys, int nsys, int32_t* iters, double* re
   status[s] = sys[s].status;
 }
 
-// Refinement: x64 = warm ? u : 0 and x32 = 0 for every node of every system.
-__global__ void k_ir_init(const __grid_constant__ Batch b, int warm) {
+// ------------------------------------------------------------------ FP64 iterative refinement
+// Augmented-system refinement of the least-squares problem min ||S x - b|| (Bjorck): the
+// solution x64 and the residual r64 = (r64 on the nodes, r2_64 on the receivers) are kept
+// in FP64; every outer step forms the FP64 residuals of the augmented system
+//     f = b - r64 - S x64,   g = -S^H r64,
+// and an FP32 CGLS inner solve of   min 1/2 ||S dx - f||^2 + Re<g, dx>   (same iterates as CGLS
+// with s = S^H r + S^H r64 = S^H r - g) returns the corrections dx and dr = f - S dx.  The kernels below
+// do the elementwise parts; b is the inner (complex64) view of the batch, with x64, r64, q64,
+// r2_64 and r2_in set.  Systems whose refinement has finished (outer_done) are left alone.
+
+struct IrU {
+  float2* u[WRI_MAXG];  // the caller's complex64 wavefields, one pointer per group
+};
+
+__device__ __forceinline__ int nsys_of(const Batch& b) { return b.g[b.ngroups - 1].sys0 + b.g[b.ngroups - 1].nsys; }
+
+// x64 = warm ? u : 0, r64 = 0, x32 = 0 on every node; r2_64 = 0 on every receiver entry.
+__global__ void k_ir_init(const __grid_constant__ Batch b, IrU U, int warm) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (int g = 0; g < b.ngroups; ++g) {
     const GroupDev& G = b.g[g];
     const long long tot = (long long)G.nsys * G.n;
-    const float2* u = (const float2*)G.d;  // caller's u (C64), passed through the d slot
+    const float2* u = U.u[g];
     double2* x64 = (double2*)G.x64;
+    double2* r64 = (double2*)G.r64;
     float2* x32 = (float2*)G.x;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-         e += (long long)gridDim.x * blockDim.x) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += stride) {
       x64[e] = warm ? make_double2(u[e].x, u[e].y) : make_double2(0.0, 0.0);
+      r64[e] = make_double2(0.0, 0.0);
       x32[e] = make_float2(0.f, 0.f);
     }
   }
+  const int ns = nsys_of(b);
+  double2* r2 = (double2*)b.r2_64;
+  for (int s = blockIdx.x; s < ns; s += gridDim.x)
+    for (int k = b.sys[s].rec_begin + threadIdx.x; k < b.sys[s].rec_end; k += blockDim.x) r2[k] = make_double2(0.0, 0.0);
 }
 
-// Refinement: x64 += x32, x32 = 0 (systems still refining), or u = (complex64) x64 (final).
-__global__ void k_ir_accum(const __grid_constant__ Batch b, int final_cast) {
+// Forcing of an outer step: inner r1[0] = q64 - r64 (= f on the nodes) and inner receiver
+// residual r2_in = q2 - r2_64, both rounded to complex64.  q = b - S x64 comes from the FP64
+// residual kernel (q2: its receiver part).
+__global__ void k_ir_forcing(const __grid_constant__ Batch b, const double2* q2) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int g = 0; g < b.ngroups; ++g) {
+    const GroupDev& G = b.g[g];
+    const long long tot = (long long)G.nsys * G.n;
+    const double2* q = (const double2*)G.q64;
+    const double2* r64 = (const double2*)G.r64;
+    float2* f = (float2*)G.r1[0];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += stride) {
+      if (b.sys[G.sys0 + (int)(e / G.n)].outer_done) continue;
+      const double2 a = q[e], r = r64[e];
+      f[e] = make_float2((float)(a.x - r.x), (float)(a.y - r.y));
+    }
+  }
+  const int ns = nsys_of(b);
+  const double2* r2 = (const double2*)b.r2_64;
+  float2* f2 = (float2*)b.r2_in;
+  for (int s = blockIdx.x; s < ns; s += gridDim.x) {
+    if (b.sys[s].outer_done) continue;
+    for (int k = b.sys[s].rec_begin + threadIdx.x; k < b.sys[s].rec_end; k += blockDim.x)
+      f2[k] = make_float2((float)(q2[k].x - r2[k].x), (float)(q2[k].y - r2[k].y));
+  }
+}
+
+// Update after an inner solve: x64 += dx (then dx = 0), r64 += dr on the nodes (the inner
+// residual of the system's last iteration sits in r1[iter & 1]) and r2_64 += r2_in.
+__global__ void k_ir_update(const __grid_constant__ Batch b) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (int g = 0; g < b.ngroups; ++g) {
     const GroupDev& G = b.g[g];
     const long long tot = (long long)G.nsys * G.n;
     double2* x64 = (double2*)G.x64;
+    double2* r64 = (double2*)G.r64;
     float2* x32 = (float2*)G.x;
-    float2* u = (float2*)G.t1;  // caller's u, passed through the t1 slot
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-         e += (long long)gridDim.x * blockDim.x) {
-      if (final_cast) {
-        const double2 v = x64[e];
-        u[e] = make_float2((float)v.x, (float)v.y);
-      } else {
-        const float2 d = x32[e];
-        if (d.x != 0.f || d.y != 0.f) {
-          double2 v = x64[e];
-          v.x += d.x;
-          v.y += d.y;
-          x64[e] = v;
-          x32[e] = make_float2(0.f, 0.f);
-        }
-      }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += stride) {
+      const SysDev& sd = b.sys[G.sys0 + (int)(e / G.n)];
+      if (sd.outer_done) continue;
+      const float2 dx = x32[e];
+      const float2 dr = ((const float2*)G.r1[sd.iter & 1])[e];
+      double2 v = x64[e];
+      v.x += dx.x;
+      v.y += dx.y;
+      x64[e] = v;
+      x32[e] = make_float2(0.f, 0.f);
+      double2 r = r64[e];
+      r.x += dr.x;
+      r.y += dr.y;
+      r64[e] = r;
+    }
+  }
+  const int ns = nsys_of(b);
+  double2* r2 = (double2*)b.r2_64;
+  const float2* d2 = (const float2*)b.r2_in;
+  for (int s = blockIdx.x; s < ns; s += gridDim.x) {
+    if (b.sys[s].outer_done) continue;
+    for (int k = b.sys[s].rec_begin + threadIdx.x; k < b.sys[s].rec_end; k += blockDim.x) {
+      double2 r = r2[k];
+      r.x += d2[k].x;
+      r.y += d2[k].y;
+      r2[k] = r;
     }
   }
 }
 
-// (A u)[node] for one node with the general coefficients (7 loads).
-template <typename R>
-__device__ cx<R> apply_at(const GroupDev& G, const cx<R>* u, long long node) {
-  const long long plane = (long long)G.nx * G.ny;
-  const int k = (int)(node / plane);
-  const long long rem = node - (long long)k * plane;
-  const int j = (int)(rem / G.nx);
-  const int i = (int)(rem - (long long)j * G.nx);
-  auto at = [&](int ii, int jj, int kk) -> cx<R> {
-    if (ii < 0 || jj < 0 || kk < 0 || ii >= G.nx || jj >= G.ny || kk >= G.nz) return czero<R>();
-    return u[(long long)kk * plane + (long long)jj * G.nx + ii];
-  };
-  const XYCoef<R> c = xy_coef<R, false>(G, i, j);
-  const ZCoef<R> z = z_coef<R, false>(G, k);
-  const R om2m = pick<R>(G.omega * G.omega, G.om2f) * model_at<R>(G.m, G.m_double, node);
-  return stencil_general<R, false>(G, c, z, om2m, at(i, j, k), at(i - 1, j, k), at(i + 1, j, k),
-                                   at(i, j - 1, k), at(i, j + 1, k), at(i, j, k - 1), at(i, j, k + 1));
+// u = x64 rounded to complex64.
+__global__ void k_ir_final(const __grid_constant__ Batch b, IrU U) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int g = 0; g < b.ngroups; ++g) {
+    const GroupDev& G = b.g[g];
+    const long long tot = (long long)G.nsys * G.n;
+    const double2* x64 = (const double2*)G.x64;
+    float2* u = U.u[g];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += stride)
+      u[e] = make_float2((float)x64[e].x, (float)x64[e].y);
+  }
 }
 
 // alpha_out[s] = (A u_s)[src_s]; one thread per system.
@@ -124,7 +180,7 @@ __global__ void k_source_estimate(const __grid_constant__ Batch b, int nsys_tota
   const SysDev& sd = b.sys[s];
   const GroupDev& G = b.g[sd.group];
   const cx<R>* u = (const cx<R>*)G.x + (long long)sd.local * G.n;
-  const cx<R> a = apply_at<R>(G, u, sd.src);
+  const cx<R> a = stencil_at<R, false>(G, u, sd.src);
   alpha_out[2 * s] = (double)a.x;
   alpha_out[2 * s + 1] = (double)a.y;
 }

@@ -673,4 +673,398 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
   }
 }
 
+// ------------------------------------------------------------------ warp-specialised phases
+// Same work, decomposition, boxes and finalizers as k_phase_tma2, with the plane pipeline
+// decoupled from the CTA barrier:
+//   * the last warp only issues the TMA copies: before refilling a stage it waits on that
+//     stage's "empty" mbarrier, which every consumer warp arrives on once it is done with the
+//     stage; consumers wait on the stage's "full" mbarrier (armed with the byte count);
+//   * consumer warps never synchronise with each other inside a tile column: a thread forms
+//     the stencil input F = a + c b of its own nodes and keeps it in registers for the three
+//     planes the z-stencil needs, and forms the in-plane neighbours' F straight from the
+//     stage's copy boxes (each F value is the same rounded a + c b wherever it is formed);
+//   * a stage is released once the stencil of its plane is done, so a CTA holds two planes
+//     and keeps S - 2 planes of copies in flight.
+// All waits are bounded: a time-out raises a CTA-wide abort flag and the error flag of the
+// launch; the other roles see the flag in their waits, every consumer warp still reaches the
+// same named barriers, and the copy warp waits (bounded) for its copies before it exits.
+template <int MODE, int BY>
+struct WsLayout {
+  static constexpr int HW = WRI_TX + 4;  // 36 columns: x0-2 .. x0+33
+  static constexpr int HH = BY + 2;
+  static constexpr int pad(int v) { return (v + 127) / 128 * 128; }
+  static constexpr int HALO = HW * HH * 8;
+  static constexpr int CTR = WRI_TX * BY * 8;
+  static constexpr int MB = WRI_TX * BY * 4;
+  static constexpr int OFF_B = pad(HALO);
+  static constexpr int OFF_X = OFF_B + pad(HALO);
+  static constexpr int OFF_M = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);
+  static constexpr int STAGE = OFF_M + pad(MB);
+  static size_t bytes(int S) { return 128 + (size_t)S * STAGE + 16 * S; }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// bounded wait that also gives up as soon as another role raised the abort flag
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
+  for (int i = 0; i < (1 << 24); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && *abort_flag) return false;
+  }
+  return false;
+}
+
+// OR of a predicate over the first NC threads (named barrier 1): the same answer in every one
+// of them, so a decision taken on it keeps them on the same barriers.
+template <int NC>
+__device__ __forceinline__ bool first_threads_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(NC)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ float2 fma_c(float c, float2 b, float2 a) {
+  return make_float2(__fmaf_rn(c, b.x, a.x), __fmaf_rn(c, b.y, a.y));
+}
+
+template <int MODE, int BY, int S, int MINB>
+__global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_constant__ Batch b,
+                                                                  const __grid_constant__ TmaSet T) {
+  static_assert(MODE == M_P1 || MODE == M_P2, "the warp-specialised path covers the two CGLS phases");
+  static_assert(S >= 3, "two stages are held by the consumers");
+  typedef float2 C;
+  typedef WsLayout<MODE, BY> L;
+  typedef FirstThreadsSync<16 * BY> CSync;
+  constexpr bool CONJ = (MODE == M_P2);
+  constexpr int NC = 16 * BY;   // consumer threads: two x-adjacent nodes each
+  constexpr int NCW = NC / 32;  // consumer warps
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red[NCW];
+  __shared__ double bcast;
+  __shared__ int s_last;
+  __shared__ volatile int s_abort;
+  __shared__ C xs_tab[WRI_TX], xh_tab[WRI_TX + 1], ys_tab[BY], yh_tab[BY + 1];
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::STAGE);
+  uint64_t* empty = full + S;
+
+  const int tid = threadIdx.x;
+  if ((smem_addr(smem) & 127u) != 0u || (L::OFF_B & 127) || (L::OFF_X & 127) || (L::OFF_M & 127) ||
+      (L::STAGE & 127)) {
+    if (tid == 0) atomicExch(T.err, 2);
+    return;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    s_abort = 0;
+  }
+  __syncthreads();  // the only CTA-wide barrier: the copy warp leaves the consumers' barriers after it
+
+  // ================================================================ copy warp
+  if (tid >= NC) {
+    if (tid != NC) return;
+    unsigned fills = 0;
+    bool stop = false;
+    for (long long item = blockIdx.x; item < b.nitems && !stop; item += gridDim.x) {
+      const int gi = find_group(b, item);
+      const GroupDev& G = b.g[gi];
+      int sl, tile;
+      item_coords(b, G, item - G.item0, sl, tile);
+      const SysDev* sd = b.sys + (G.sys0 + sl);
+      const int state = sd->state;
+      if (MODE == M_P1 ? (state == ST_DONE) : (state != ST_ACTIVE)) continue;
+      if (MODE == M_P1 && state == ST_FINISHING) continue;  // x-only pass: no copies
+      const int tzi = tile % G.zsplit;
+      const int txy = tile / G.zsplit;
+      const int x0 = (txy % G.tiles_x) * WRI_TX;
+      const int y0 = (txy / G.tiles_x) * BY;
+      const int z0 = tzi * G.zc;
+      const int z1 = min(z0 + G.zc, G.nz);
+      const int iter = sd->iter;
+      const int cur = iter & 1;
+      const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
+      const bool hasB = (MODE == M_P2) || iter > 0;
+      const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
+      const bool hasX = (MODE == M_P1) && iter > 0;
+      const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + L::MB;
+      const int count = z1 - z0 + 2;
+      for (int q = 0; q < count; ++q, ++fills) {
+        const int st = (int)(fills % S);
+        if (fills >= (unsigned)S && !mbar_wait_or_abort(&empty[st], ((fills / S) - 1) & 1u, &s_abort)) {
+          s_abort = 1;
+          atomicExch(T.err, 1);
+          stop = true;
+          break;
+        }
+        if (s_abort) {
+          stop = true;
+          break;
+        }
+        unsigned char* base = smem + (size_t)st * L::STAGE;
+        const int kq = z0 - 1 + q;
+        mbar_expect_tx(&full[st], tx_bytes);
+        tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
+        if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &full[st]);
+        if (hasX) tma_load_4d(base + L::OFF_X, &T.map[gi][TM_X], x0, y0, kq, sl, &full[st]);
+        tma_load_3d(base + L::OFF_M, &T.map[gi][TM_M], x0, y0, kq, &full[st]);
+      }
+    }
+    if (stop) {
+      // wait (bounded) until every copy issued into the ring has landed
+      const unsigned first = fills > (unsigned)S ? fills - S : 0u;
+      for (unsigned u = first; u < fills; ++u) mbar_wait(&full[u % S], (u / S) & 1u);
+    }
+    return;
+  }
+
+  // ================================================================ consumer warps
+  const int lane = tid & 31;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int o = (ty + 1) * L::HW + 2 * tx + 2;  // own pair in a halo box
+  const int oc = ty * WRI_TX + 2 * tx;          // own pair in a 32 x BY box
+  unsigned fills = 0;
+
+  for (long long item = blockIdx.x; item < b.nitems; item += gridDim.x) {
+    const int gi = find_group(b, item);
+    const GroupDev& G = b.g[gi];
+    int sl, tile;
+    item_coords(b, G, item - G.item0, sl, tile);
+    SysDev* sd = b.sys + (G.sys0 + sl);
+    const int state = sd->state;
+    if (MODE == M_P1 ? (state == ST_DONE) : (state != ST_ACTIVE)) continue;
+    const bool xonly = (MODE == M_P1 && state == ST_FINISHING);
+
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int tzi = tile % G.zsplit;
+    const int txy = tile / G.zsplit;
+    const int x0 = (txy % G.tiles_x) * WRI_TX;
+    const int y0 = (txy / G.tiles_x) * BY;
+    const int z0 = tzi * G.zc;
+    const int z1 = min(z0 + G.zc, nz);
+    const int i0 = x0 + 2 * tx, j = y0 + ty;
+    const bool own = (i0 < nx) && (j < ny);  // nx is even: the pair is in or out as a whole
+    const long long plane = (long long)nx * ny;
+    const long long col = (long long)j * nx + i0;
+    const long long off = (long long)sl * G.n;
+    const int iter = sd->iter;
+    const int cur = iter & 1;
+    double accd = 0.0;
+
+    if (xonly) {
+      C* X = (C*)G.x + off + col;
+      const C* Pc = (const C*)G.p[cur] + off + col;
+      const float a = (float)sd->alpha;
+      if (own)
+        for (int k = z0; k < z1; ++k) {
+          const long long q = k * plane;
+          const float4 xv = ld4(X + q), pv = __ldg(reinterpret_cast<const float4*>(Pc + q));
+          st4(X + q, lo2(xv) + a * lo2(pv), hi2(xv) + a * hi2(pv));
+        }
+    } else {
+      const bool hasB = (MODE == M_P2) || iter > 0;
+      const bool hasX = (MODE == M_P1) && iter > 0;
+      const float coef = (MODE == M_P1) ? (float)sd->beta : -(float)sd->alpha;
+      const float xal = (float)sd->alpha;
+      C* pF = ((MODE == M_P1) ? (C*)G.p[cur ^ 1] : (C*)G.r1[cur ^ 1]) + off + col;
+      C* pX = (C*)G.x + off + col;
+      C* pO = ((MODE == M_P1) ? (C*)G.t1 : (C*)G.s) + off + col;
+      const C* pG = (MODE == M_P2 && G.gvec) ? (const C*)G.gvec + off + col : nullptr;
+      int src_k = -1;
+      long long src_col = -1;
+      if (MODE == M_P1 && G.masked) {
+        src_k = (int)(sd->src / plane);
+        src_col = sd->src - (long long)src_k * plane;
+      }
+      const int src_lane = (src_col == col) ? 0 : (src_col == col + 1) ? 1 : -1;
+      const int count = z1 - z0 + 2;
+
+      int xlo, xhi, ylo, yhi, zlo, zhi;
+      interior_range(G.ax, xlo, xhi);
+      interior_range(G.ay, ylo, yhi);
+      interior_range(G.az, zlo, zhi);
+      const int xpf = ((x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi)) ? 0 : 4;
+      const int ypf = ((y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi)) ? 0 : 2;
+      if (xpf | ypf) {
+        const float ih2t = G.ih2f;
+        for (int e = tid; e < 2 * WRI_TX + 2 * BY + 2; e += NC) {
+          if (e < WRI_TX) {
+            xs_tab[e] = stretch_at<float, CONJ>(G.ax, float(x0 + e));
+          } else if (e < 2 * WRI_TX + 1) {
+            const int c = e - WRI_TX;
+            xh_tab[c] = ih2t * inv(stretch_at<float, CONJ>(G.ax, float(x0 + c) - 0.5f));
+          } else if (e < 2 * WRI_TX + 1 + BY) {
+            const int r = e - 2 * WRI_TX - 1;
+            ys_tab[r] = stretch_at<float, CONJ>(G.ay, float(y0 + r));
+          } else {
+            const int r = e - 2 * WRI_TX - 1 - BY;
+            yh_tab[r] = ih2t * inv(stretch_at<float, CONJ>(G.ay, float(y0 + r) - 0.5f));
+          }
+        }
+        CSync::sync();  // tables complete (the previous item's readers passed its final barrier)
+      }
+      const float om2 = G.om2f;
+      const float ih2 = G.ih2f;
+      const float2* ztab = G.ztab + (CONJ ? 3 * nz : 0);
+
+      CompSum acc;
+      C fm0 = czero<float>(), fm1 = fm0, fc0 = fm0, fc1 = fm0;  // own F of planes kq-2, kq-1
+      float2 m_c = make_float2(0.f, 0.f);                        // m of plane kq-1
+      long long po = (long long)(z0 - 1) * plane;
+      for (int q = 0; q < count; ++q, po += plane) {
+        const unsigned u = fills + q;
+        const int st = (int)(u % S);
+        bool ok = true;
+        if (!s_abort) {
+          ok = mbar_wait_or_abort(&full[st], (u / S) & 1u, &s_abort);
+          if (!ok) {
+            s_abort = 1;
+            atomicExch(T.err, 1);
+          }
+        } else {
+          ok = false;
+        }
+        C v0 = czero<float>(), v1 = v0;
+        float2 m_new = make_float2(0.f, 0.f);
+        if (ok) {
+          const unsigned char* base = smem + (size_t)st * L::STAGE;
+          const C* A = reinterpret_cast<const C*>(base);
+          const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
+          const int kq = z0 - 1 + q;
+          const bool mine = own && kq >= z0 && kq < z1;
+          const float4 a = ld4(A + o);
+          v0 = lo2(a);
+          v1 = hi2(a);
+          if (hasB) {
+            const float4 bb = ld4(B + o);
+            v0 = fma_c(coef, lo2(bb), v0);
+            v1 = fma_c(coef, hi2(bb), v1);
+            if (MODE == M_P1 && hasX && mine) {
+              const float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
+              st4(pX + po, fma_c(xal, lo2(bb), lo2(xv)), fma_c(xal, hi2(bb), hi2(xv)));
+            }
+          }
+          if (mine) st4(pF + po, v0, v1);
+          m_new = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base + L::OFF_M) + oc);
+          if (q >= 2) {
+            // stencil of plane kp = kq - 1: z neighbours from registers, in-plane neighbours
+            // formed from the copy boxes of plane kp
+            const int kp = kq - 1;
+            const unsigned char* bp = smem + (size_t)((u - 1) % S) * L::STAGE;
+            const C* Ap = reinterpret_cast<const C*>(bp);
+            const C* Bp = reinterpret_cast<const C*>(bp + L::OFF_B);
+            C l = Ap[o - 1], r = Ap[o + 2];
+            float4 ym = ld4(Ap + o - L::HW), yp = ld4(Ap + o + L::HW);
+            C ym0 = lo2(ym), ym1 = hi2(ym), yp0 = lo2(yp), yp1 = hi2(yp);
+            if (hasB) {
+              l = fma_c(coef, Bp[o - 1], l);
+              r = fma_c(coef, Bp[o + 2], r);
+              const float4 bym = ld4(Bp + o - L::HW), byp = ld4(Bp + o + L::HW);
+              ym0 = fma_c(coef, lo2(bym), ym0);
+              ym1 = fma_c(coef, hi2(bym), ym1);
+              yp0 = fma_c(coef, lo2(byp), yp0);
+              yp1 = fma_c(coef, hi2(byp), yp1);
+            }
+            C a0, a1;
+            const int var = xpf | ypf | ((kp >= zlo && kp <= zhi) ? 0 : 1);
+            if (var == 0) {
+              a0 = stencil_interior<float>(ih2, om2 * m_c.x, fc0, l, fc1, ym0, yp0, fm0, v0);
+              a1 = stencil_interior<float>(ih2, om2 * m_c.y, fc1, fc0, r, ym1, yp1, fm1, v1);
+            } else {
+              C sx0 = mkc(1.f, 0.f), sx1 = sx0, ixa = mkc(ih2, 0.f), ixb = ixa, ixc = ixa;
+              C sy = mkc(1.f, 0.f), iym = mkc(ih2, 0.f), iyp = iym;
+              C sz = mkc(1.f, 0.f), izm = mkc(ih2, 0.f), izp = izm;
+              if (var & 4) {
+                sx0 = xs_tab[2 * tx];
+                sx1 = xs_tab[2 * tx + 1];
+                ixa = xh_tab[2 * tx];
+                ixb = xh_tab[2 * tx + 1];
+                ixc = xh_tab[2 * tx + 2];
+              }
+              if (var & 2) {
+                sy = ys_tab[ty];
+                iym = yh_tab[ty];
+                iyp = yh_tab[ty + 1];
+              }
+              if (var & 1) {
+                const C* zr = ztab + 3 * kp;
+                sz = __ldg(zr);
+                izm = __ldg(zr + 1);
+                izp = __ldg(zr + 2);
+              }
+              const float om0 = om2 * m_c.x, om1 = om2 * m_c.y;
+#define WRI_AX(AX_, AY_, AZ_)                                                                                  \
+  a0 = stencil_axes<AX_, AY_, AZ_>(ih2, om0, fc0, l, fc1, ym0, yp0, fm0, v0, sx0, ixa, ixb, sy, iym, iyp, sz, izm, \
+                                   izp);                                                                       \
+  a1 = stencil_axes<AX_, AY_, AZ_>(ih2, om1, fc1, fc0, r, ym1, yp1, fm1, v1, sx1, ixb, ixc, sy, iym, iyp, sz, izm, \
+                                   izp);
+              switch (var) {
+                case 1: WRI_AX(false, false, true) break;
+                case 2: WRI_AX(false, true, false) break;
+                case 3: WRI_AX(false, true, true) break;
+                case 4: WRI_AX(true, false, false) break;
+                case 5: WRI_AX(true, false, true) break;
+                case 6: WRI_AX(true, true, false) break;
+                default: WRI_AX(true, true, true) break;
+              }
+#undef WRI_AX
+            }
+            if (own) {
+              if (MODE == M_P1 && kp == src_k) {
+                if (src_lane == 0) a0 = czero<float>();
+                if (src_lane == 1) a1 = czero<float>();
+              }
+              if (MODE == M_P2 && pG) {
+                // refinement inner solve: s = S^H r + S^H r64
+                const float4 gv = __ldg(reinterpret_cast<const float4*>(pG + po - plane));
+                a0 = a0 + lo2(gv);
+                a1 = a1 + hi2(gv);
+              }
+              st4(pO + po - plane, a0, a1);
+              acc.add(abs2(a0));
+              acc.add(abs2(a1));
+            }
+          }
+        }
+        if (q >= 1) {
+          // plane kq-1 is done: hand its stage back to the copy warp
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[(u - 1) % S]);
+        }
+        fm0 = fc0;
+        fm1 = fc1;
+        fc0 = v0;
+        fc1 = v1;
+        m_c = m_new;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[(fills + count - 1) % S]);
+      fills += (unsigned)count;
+      accd = acc.value();
+    }
+
+    // ---- tile partial, ticket and the system's finalizer (consumer threads only)
+    const double tsum = block_sum<NC, CSync>(accd, red);
+    // the copy warp may raise the flag at any time: decide on one reduced value
+    if (first_threads_any<NC>(s_abort != 0)) break;
+    if (tid == 0 && !xonly) b.partial[sd->part_off + tile] = tsum;
+    __threadfence();
+    CSync::sync();
+    if (tid == 0) {
+      const unsigned t = atomicAdd(&sd->ticket, 1u);
+      s_last = (t == (unsigned)(G.ntiles - 1));
+    }
+    CSync::sync();
+    if (s_last) finalize<float, float, MODE, NC, CSync>(b, G, sd, sl, xonly, red, &bcast);
+  }
+}
+
 }  // namespace wri

@@ -302,10 +302,13 @@ def workload_c3() -> Group:
     return grp
 
 
-def workload_c4(nsrc: int = 128, freqs=((3.0, 64), (5.0, 96), (8.0, 128)), nrec: int = 96) -> list:
+def workload_c4(nsrc: int = 128, freqs=((3.0, 64), (5.0, 96), (8.0, 128)), nrec: int = 96,
+                shard: int = 0) -> list:
     """Frequency-dependent grids over a 2560 m cube: 3 Hz 64^3 (h=40), 5 Hz 96^3
     (h=26.67), 8 Hz 128^3 (h=20), each + 10 PML; 128 surface sources (8x16 grid),
-    96 borehole receivers, layered + anomaly model (seed 4)."""
+    96 borehole receivers, layered + anomaly model (seed 4).  ``shard`` > 0 draws the
+    weights and traces of another shot record over the same geometry (seeds offset by
+    1000 * shard), the share of one rank in a job of several such records."""
     out = []
     extent = 2560.0
     for j, (f, n) in enumerate(freqs):
@@ -318,9 +321,9 @@ def workload_c4(nsrc: int = 128, freqs=((3.0, 64), (5.0, 96), (8.0, 128)), nrec:
         zs = np.unique(np.linspace(2, n - 3, nrec).round().astype(int))
         rec = borehole_receivers(g, n // 2 + 1, n // 2 + 1, zs)
         off, idx = _shared_receivers(len(src), rec)
-        al = source_weights(len(src), 400 + j)
+        al = source_weights(len(src), 400 + j + 1000 * shard)
         grp = Group(g, f, v, src, off, idx, default_lambda(h), float(v.max()), alpha=al)
-        grp.d = synthetic_traces(g, src, off, idx, f, 2000.0, al, seed=410 + j)
+        grp.d = synthetic_traces(g, src, off, idx, f, 2000.0, al, seed=410 + j + 1000 * shard)
         out.append(grp)
     return out
 

@@ -88,16 +88,17 @@ def test_fixed_iterations_match_oracle_cgls(W, dtype, tol, source_free):
         assert abs(rr.cpu().numpy()[s] - rr_k) <= max(tol, 1e-6) * rr_k * 10
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("cfg", list(range(14)))
 @pytest.mark.parametrize("source_free", [True, False])
 def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
-    """TMA-pipelined phases (x extent a multiple of 4): ragged 32 x BY tiles, iterates of
-    k CGLS steps equal the oracle's and the z-march kernels' (same tile height)."""
+    """TMA-pipelined phases (x extent a multiple of 4; configurations 9-13 are the
+    warp-specialised kernels): ragged 32 x BY tiles, iterates of k CGLS steps equal the
+    oracle's and the z-march kernels' (same tile height)."""
     G = case(nphys=(36, 13, 10), npml=4, nsys=3)
     m, d, al = seen(G, True)
     A = oracle_A(G, m)
     k = 25
-    by = 16 if cfg in (2, 3, 4, 5) else 8
+    by = 16 if cfg in (2, 3, 4, 5, 12) else 8
     s_t, s_m = _spec(W, G, 0, source_free), _spec(W, G, 0, source_free)
     it_t, rr_t, st_t = W.solve([s_t], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_TMA(cfg)))
     it_m, rr_m, st_m = W.solve([s_m], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_MARCH,
@@ -113,13 +114,14 @@ def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
         assert rel(u_t[s], x_k) < 3e-4
 
 
-def test_tma_z_chunks_and_convergence(W):
+@pytest.mark.parametrize("cfg", [0, 8, 9])
+def test_tma_z_chunks_and_convergence(W, cfg):
     """TMA path with z-chunks and a real stopping test: same iterations (within 5 %) and
     wavefields as the z-march kernels at tolerance 1e-3."""
     G = case(nphys=(28, 16, 14), npml=4, nsys=2)
     s_t, s_m = _spec(W, G, 0), _spec(W, G, 0)
     it_t, rr_t, st_t = W.solve([s_t], W.make_opts(tol=1e-3, max_iter=100000, dtype=0, zsplit=3,
-                                                 kernel=W.KERNEL_TMA(0)))
+                                                 kernel=W.KERNEL_TMA(cfg)))
     it_m, rr_m, st_m = W.solve([s_m], W.make_opts(tol=1e-3, max_iter=100000, dtype=0, zsplit=3,
                                                  kernel=W.KERNEL_MARCH))
     assert st_t.cpu().tolist() == [0, 0]
@@ -149,8 +151,6 @@ def test_converged_c128_matches_exact(W, source_free):
         assert rel(u[s], _exact(G, G.m, G.d, source_free, s)) < 1e-5
 
 
-@pytest.mark.xfail(reason="refinement inner solve is CG on the normal equations; diverges once kappa^2*eps32 ~ 1 "
-                          "(augmented-system refinement with CGLS inner solves replaces it)", strict=False)
 @pytest.mark.parametrize("source_free", [True, False])
 def test_mixed_precision_refinement_matches_exact(W, source_free):
     """FP32 complex stencil + FP64 refinement reaches the FP64 solution of the problem
@@ -168,9 +168,10 @@ def test_mixed_precision_refinement_matches_exact(W, source_free):
 
 
 @pytest.mark.parametrize("k", [5, 25])
-def test_first_refinement_step_is_cg_on_normal_equations(W, k):
-    """One refinement step from x = 0 with k inner FP32 iterations of CG on the
-    normal equations has the iterate of k CGLS iterations (same Krylov iterate)."""
+def test_first_refinement_step_is_cgls(W, k):
+    """The first outer step of the augmented-system refinement starts from r64 = 0, x64 = 0,
+    so its inner solve is plain CGLS on b: k inner iterations give the k-th CGLS iterate, and
+    the reported residual is the FP64 normal-equation residual of that iterate."""
     G = case(nphys=(15, 11, 9), npml=3, nsys=2, freq=15.0)
     m, d, al = seen(G, True)
     A = oracle_A(G, m)
@@ -245,8 +246,6 @@ def test_source_estimate_and_gradient_on_given_fields(W, dtype, tol, source_free
     assert abs(f.item() - f_ref) <= 10 * tol * abs(f_ref)
 
 
-@pytest.mark.xfail(reason="refinement inner solve is CG on the normal equations; diverges once kappa^2*eps32 ~ 1 "
-                          "(augmented-system refinement with CGLS inner solves replaces it)", strict=False)
 def test_pipeline_gradient_matches_oracle(W):
     """Solve + estimate + gradient (C64 with FP64 refinement) against the oracle's
     exact evaluation of f4 and g4."""
@@ -288,6 +287,31 @@ def test_batched_equals_unbatched_and_multi_group(W):
         assert np.array_equal(a, b)           # same tiles, same reduction order: bit-identical
     assert it.cpu().tolist() == [x[1] for x in ub]
     assert np.array_equal(rr.cpu().numpy(), np.array([x[2] for x in ub]))
+
+
+@pytest.mark.parametrize("kernel", [0, 2 + 9])
+def test_tma_batch_of_groups_equals_single_systems(W, kernel):
+    """Two frequency groups on different grids (x extents multiples of 4) in one batched TMA
+    solve, several orders of the work items: every system's iterate equals its own unbatched
+    z-march solve (same reduction order per system, so to rounding of the FP32 stencil)."""
+    G1 = case(nphys=(28, 12, 10), npml=4, nsys=3, seed=5)
+    G2 = case(nphys=(16, 19, 8), npml=4, nsys=5, seed=8, freq=9.0)
+    k = 20
+    for order in (0, 1, 3, 6):
+        s1, s2 = _spec(W, G1, 0), _spec(W, G2, 0)
+        it, rr, st = W.solve([s1, s2], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=kernel, order=order))
+        assert it.cpu().tolist() == [k] * 8
+        got = list(s1.u.cpu().numpy()) + list(s2.u.cpu().numpy())
+        i = 0
+        for G in (G1, G2):
+            for s in range(G.nsys):
+                one = synth.Group(G.spec, G.freq, G.v, G.src[s:s + 1], np.array([0, G.rec_off[s + 1] - G.rec_off[s]],
+                                  np.int32), G.rec_idx[G.rec_off[s]:G.rec_off[s + 1]], G.lam, G.v_max, G.pml_R,
+                                  G.alpha[s:s + 1], G.d[G.rec_off[s]:G.rec_off[s + 1]])
+                sp1 = _spec(W, one, 0)
+                W.solve([sp1], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_MARCH))
+                assert rel(got[i], sp1.u.cpu().numpy()[0]) < 1e-5, (order, i)
+                i += 1
 
 
 def test_plain_path_matches_fused(W):

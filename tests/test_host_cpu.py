@@ -1,0 +1,86 @@
+"""Host-side logic that needs no GPU: the source sharding and gradient sum of the multi-rank
+path (two gloo ranks on CPU), and the chunking of the autograd objective."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_shard_partitions_every_count():
+    from paper_2410_18429_gb300.parallel_sum import shard
+    for n in (0, 1, 7, 128, 384):
+        for world in (1, 2, 3, 8):
+            parts = [shard(n, r, world) for r in range(world)]
+            assert parts[0][0] == 0 and parts[-1][1] == n
+            for (b0, e0), (b1, e1) in zip(parts, parts[1:]):
+                assert e0 == b1
+            sizes = [e - b for b, e in parts]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+
+    from paper_2410_18429_gb300.parallel_sum import allreduce_gradient, shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # each rank owns a shard of 10 systems; its gradient is the sum of per-system terms
+    b, e = shard(10, rank, world)
+    per_system = [torch.arange(12, dtype=torch.float64).reshape(2, 2, 3) * (s + 1) for s in range(10)]
+    g = [sum(per_system[b:e], torch.zeros(2, 2, 3, dtype=torch.float64))]
+    f = torch.tensor([float(sum(s + 1 for s in range(b, e)))], dtype=torch.float64)
+    allreduce_gradient(g, f)
+    torch.save({"g": g[0], "f": f}, os.path.join(out_dir, f"r{rank}.pt"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gradient_allreduce_two_gloo_ranks(tmp_path):
+    """World size 2 on CPU: the summed gradient equals the gradient of all systems on one rank."""
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    want_g = torch.arange(12, dtype=torch.float64).reshape(2, 2, 3) * sum(range(1, 11))
+    for r in range(2):
+        got = torch.load(os.path.join(tmp_path, f"r{r}.pt"))
+        assert torch.equal(got["g"], want_g)
+        assert got["f"].item() == 55.0
+
+
+def test_allreduce_is_identity_without_process_group():
+    from paper_2410_18429_gb300.parallel_sum import allreduce_gradient
+    g = [torch.ones(3, dtype=torch.float64)]
+    f = torch.tensor([2.0], dtype=torch.float64)
+    allreduce_gradient(g, f)
+    assert torch.equal(g[0], torch.ones(3, dtype=torch.float64)) and f.item() == 2.0
+
+
+def test_objective_chunks_cover_systems():
+    from paper_2410_18429_gb300.objective import chunks
+    assert chunks(0, 4) == []
+    assert chunks(5, 2) == [(0, 2), (2, 4), (4, 5)]
+    assert chunks(3, 1 << 30) == [(0, 3)]
+    for n in range(0, 20):
+        for k in (1, 3, 7, 50):
+            c = chunks(n, k)
+            assert sum(e - b for b, e in c) == n and all(0 < e - b <= k for b, e in c)
+    with pytest.raises(ValueError):
+        chunks(3, 0)
+
+
+def test_workload_shards_differ_only_in_weights_and_data():
+    """Rank r's shot record shares the geometry and model of rank 0 but not its weights or traces."""
+    import synth
+    a = synth.workload_c4(nsrc=4, freqs=((3.0, 16),), nrec=8, shard=0)[0]
+    b = synth.workload_c4(nsrc=4, freqs=((3.0, 16),), nrec=8, shard=1)[0]
+    assert np.array_equal(a.src, b.src) and np.array_equal(a.rec_idx, b.rec_idx) and np.array_equal(a.m, b.m)
+    assert not np.allclose(a.alpha, b.alpha) and not np.allclose(a.d, b.d)
