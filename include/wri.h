@@ -93,6 +93,13 @@ typedef struct {
   const double* alpha;      /* device [2*nsys] known weights (complex128) or NULL = source-free */
   double lambda;            /* data weight, > 0 */
   void* u;                  /* device [nsys][n] complex (dtype): in = x0 if warm_start, out = u */
+  void* u64;                /* WRI_C64 only, optional: device [nsys][n] complex128 (16-byte aligned)
+                               or NULL.  wri_solve_batch also writes the solution here, in FP64
+                               (the refinement's FP64 master; without refinement, u widened), and
+                               wri_source_estimate / wri_gradient then read it instead of u and use
+                               FP64 stencils: the gradient needs the PDE residual A u - a e, which
+                               rounding u to complex64 would swamp.  In one call either every
+                               group sets it or none does.  Ignored for WRI_C128. */
 } wri_group;
 
 typedef struct {
@@ -111,7 +118,8 @@ typedef struct {
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
   int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
-                          1 = z-march kernels only, 2 + c = TMA configuration c (0..8) */
+                          1 = z-march kernels only, 2 + c = TMA configuration c (0..13; 9..13
+                          are the warp-specialised kernels); see wri_autotune */
   int32_t order;       /* TMA phases: 0 = automatic, 1 = tiles of a system consecutive,
                           2 = systems of a tile consecutive, 3 = z-chunk slowest,
                           4 / 5 / 6 = blocks of 4 / 8 / 16 systems, tiles in order */
@@ -184,6 +192,21 @@ WRI_API int wri_gradient(const wri_group* groups, int ngroups, int dtype, const 
 #define WRI_NOALLOC_SCRATCH_BYTES (4u << 20)
 WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype, const double* alpha_in,
                                  double* const* grad, double* f, wri_stream_t stream);
+
+/* Autotuner of the batched solve (an interface outside the paper, which prescribes no
+ * kernel configuration).  For a complex64 batch without refinement it times `trial_iters`
+ * CGLS iterations (>= 2) of every candidate pair (TMA configuration, work-item order) on the
+ * caller's own batch, on `stream`, and writes the fastest into opts->kernel and opts->order
+ * (other fields unchanged).  Candidates whose workspace exceeds ws_bytes are skipped.
+ *   - groups[g].u is used as the iterate of the trial solves: its contents are overwritten.
+ *   - The choice is cached for the process, keyed by the device, the grids, the system counts
+ *     and the receiver counts: a repeated call for the same batch shape returns the cached
+ *     choice without timing anything (and without touching u).
+ *   - Batches the TMA phases cannot take (complex128, refinement, the unfused baseline, an x
+ *     extent that is not a multiple of 4) keep opts unchanged and return WRI_OK.
+ *   - Synchronises `stream` (it reads event timings on the host). */
+WRI_API int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int trial_iters,
+                         void* workspace, size_t ws_bytes, wri_stream_t stream);
 
 /* Number of built tile configurations and the thread-block shape of one of them. */
 WRI_API int wri_tile_count(void);

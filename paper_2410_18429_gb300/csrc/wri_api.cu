@@ -21,11 +21,12 @@ using namespace wri;
 namespace {
 
 constexpr int kRefSMs = 152;  // SMs of a GB300; sets the z-split of small batches
-// Measured defaults of the TMA phases on GB300 (128 sources x 3 frequency grids):
-// two nodes per thread, 32 x 8 tiles, 4 stages, 4 CTAs/SM; work items in blocks of
-// 16 systems (neighbouring tiles of a system run together, so their halos meet in L2);
-// L2 fills of 64 bytes on a copy miss (128-byte fills over-fetch the halo columns).
-constexpr int kDefaultTmaCfg = 8;
+// Measured defaults of the TMA phases on GB300 (128 sources x 3 frequency grids): the
+// warp-specialised kernel (a copy warp and 4 consumer warps, two nodes per thread, 32 x 8
+// tiles, 4 stages, 4 CTAs/SM); work items in blocks of 16 systems (neighbouring tiles of a
+// system run together, so their halos meet in L2); L2 fills of 64 bytes on a copy miss
+// (128-byte fills over-fetch the halo columns).  wri_autotune refines the choice per batch.
+constexpr int kDefaultTmaCfg = 9;
 constexpr int kDefaultOrder = 6;
 constexpr int kDefaultPromotion = 2;
 constexpr size_t kAlign = 256;
@@ -152,7 +153,7 @@ struct Plan {
   size_t aux_total = 0, total = 0;
   GroupDev g[WRI_MAXG];
   size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][2], v_s[WRI_MAXG], v_t1[WRI_MAXG];
-  size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG], v_q64[WRI_MAXG], v_g32[WRI_MAXG];
+  size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG], v_q64[WRI_MAXG], v_g32[WRI_MAXG], v_rmap[WRI_MAXG];
   size_t off_ztab[WRI_MAXG];
   std::vector<int> rec_base;  // first receiver entry of every group
 };
@@ -244,7 +245,7 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
     P.v_p[gi][1] = off; off += vb;
     P.v_s[gi] = off; off += vb;
     P.v_t1[gi] = off; off += vb;
-    P.v_x32[gi] = P.v_x64[gi] = P.v_r64[gi] = P.v_q64[gi] = P.v_g32[gi] = 0;
+    P.v_x32[gi] = P.v_x64[gi] = P.v_r64[gi] = P.v_q64[gi] = P.v_g32[gi] = P.v_rmap[gi] = 0;
     if (P.ir) {
       const size_t nn = (size_t)P.g[gi].nsys * (size_t)P.g[gi].n;
       P.v_x32[gi] = off; off += align_up(8 * nn);
@@ -252,6 +253,7 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
       P.v_r64[gi] = off; off += align_up(16 * nn);
       P.v_q64[gi] = off; off += align_up(16 * nn);
       P.v_g32[gi] = off; off += align_up(8 * nn);
+      P.v_rmap[gi] = off; off += align_up(4 * nn);
     }
   }
   P.total = off;
@@ -313,6 +315,11 @@ struct DevCtx {
 };
 std::mutex g_mu;
 DevCtx g_ctx[64];
+struct Tuned {
+  std::vector<long long> key;  // device, groups, then per group nx, ny, nz, nsys, receivers
+  int kernel, order;
+};
+std::vector<Tuned> g_tuned;  // choices of wri_autotune, guarded by g_mu
 
 DevCtx* ctx() {
   int dev = 0;
@@ -581,7 +588,10 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
   for (int gi = 0; gi < P.ngroups; ++gi) {
     outer.g[gi].x = outer.g[gi].x64;
     outer.g[gi].r1[0] = outer.g[gi].q64;
+    outer.g[gi].rmap = (const int*)(ws + P.v_rmap[gi]);
+    WRI_CK(cudaMemsetAsync(ws + P.v_rmap[gi], 0xff, 4 * (size_t)P.g[gi].nsys * (size_t)P.g[gi].n, st));
   }
+  WRI_CK(launch_ir_rmap(outer, P.nsys_total, st));
   outer.max_iter = o->max_iter;
   outer.tol = o->tol;
   outer.refine_tol = o->refine_tol;
@@ -789,8 +799,25 @@ int apply_common(const wri_grid* grid, int dtype, const void* m, int nsys, const
   return WRI_OK;
 }
 
+// Precision of the source estimate / gradient: complex128 problems and complex64 problems whose
+// groups all carry an FP64 wavefield (u64) run FP64 kernels (*wide); u64 on some groups only is an error.
+int aux_precision(const wri_group* groups, int ngroups, int dtype, bool* wide) {
+  int with = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    if (groups[gi].u64 && ((uintptr_t)groups[gi].u64 % 16) != 0) return WRI_EINVAL;
+    with += groups[gi].u64 ? 1 : 0;
+  }
+  if (dtype == WRI_C128) {
+    *wide = false;
+    return WRI_OK;
+  }
+  if (with != 0 && with != ngroups) return WRI_EINVAL;
+  *wide = with == ngroups;
+  return WRI_OK;
+}
+
 // geometry-only batch for the source estimate / gradient
-Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, int dtype) {
+Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, int dtype, bool wide = false) {
   Batch b;
   std::memset(&b, 0, sizeof(b));
   b.ngroups = ngroups;
@@ -810,7 +837,7 @@ Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, i
     G.m = groups[gi].m;
     G.m_double = dtype == WRI_C128 ? 1 : 0;
     G.d = groups[gi].d;
-    G.x = groups[gi].u;
+    G.x = wide ? groups[gi].u64 : groups[gi].u;
     // gradient decomposition: one work item per tile, systems looped inside
     G.tiles_x = (G.nx + WRI_TX - 1) / WRI_TX;
     G.tiles_y = (G.ny + 7) / 8;
@@ -859,6 +886,9 @@ int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype, const 
   if (!alpha_in || !grad || !f) return WRI_EINVAL;
   for (int gi = 0; gi < ngroups; ++gi)
     if (!grad[gi]) return WRI_EINVAL;
+  bool wide = false;
+  rc = aux_precision(groups, ngroups, dtype, &wide);
+  if (rc != WRI_OK) return rc;
   Plan P;
   plan_aux(groups, ngroups, P);
   if (P.aux_total > (size_t)WRI_NOALLOC_SCRATCH_BYTES) return WRI_ESCRATCH;
@@ -868,15 +898,15 @@ int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype, const 
   cudaStream_t st = (cudaStream_t)stream;
   rc = upload(groups, ngroups, P, ws, st);  // overwrites every byte the kernels read
   if (rc != WRI_OK) return rc;
-  Batch b = aux_batch(groups, ngroups, P, ws, dtype);
+  Batch b = aux_batch(groups, ngroups, P, ws, dtype, wide);
   b.f = f;
   for (int gi = 0; gi < ngroups; ++gi) {
     b.g[gi].alpha = alpha_in + 2 * b.g[gi].sys0;
     b.g[gi].grad = grad[gi];
   }
-  const int rb = dtype == WRI_C128 ? 8 : 4;
+  const int rb = (dtype == WRI_C128 || wide) ? 8 : 4;
   WRI_CK(march(rb, rb, M_GRAD, false, 8, b, st));
-  WRI_CK(launch_data_term(rb, b, P.nsys_total, st));
+  WRI_CK(launch_data_term(rb, dtype == WRI_C128 ? 8 : 4, b, P.nsys_total, st));
   return WRI_OK;
 }
 
@@ -912,6 +942,8 @@ int wri_solve_batch(const wri_group* groups, int ngroups, const wri_solve_opts* 
   rc = validate_groups(groups, ngroups, true);
   if (rc != WRI_OK) return rc;
   if (!iters || !relres || !status) return WRI_EINVAL;
+  for (int gi = 0; gi < ngroups; ++gi)
+    if (groups[gi].u64 && ((uintptr_t)groups[gi].u64 % 16) != 0) return WRI_EINVAL;
   Plan P;
   plan_solve(groups, ngroups, opts, P);
   rc = check_ws(P, workspace, ws_bytes);
@@ -920,10 +952,23 @@ int wri_solve_batch(const wri_group* groups, int ngroups, const wri_solve_opts* 
   char* ws = (char*)workspace;
   rc = upload(groups, ngroups, P, ws, st);
   if (rc != WRI_OK) return rc;
-  if (opts->plain) return solve_plain(groups, ngroups, opts, P, ws, iters, relres, status, st);
-  rc = P.ir ? solve_refined(groups, ngroups, opts, P, ws, st) : solve_fused(groups, ngroups, opts, P, ws, st);
+  if (opts->plain) {
+    rc = solve_plain(groups, ngroups, opts, P, ws, iters, relres, status, st);
+  } else {
+    rc = P.ir ? solve_refined(groups, ngroups, opts, P, ws, st) : solve_fused(groups, ngroups, opts, P, ws, st);
+    if (rc == WRI_OK)
+      WRI_CK(launch_export((const SysDev*)(ws + P.off_sys), P.nsys_total, iters, relres, status, st));
+  }
   if (rc != WRI_OK) return rc;
-  WRI_CK(launch_export((const SysDev*)(ws + P.off_sys), P.nsys_total, iters, relres, status, st));
+  if (opts->dtype == WRI_C64)  // the FP64 wavefield output
+    for (int gi = 0; gi < ngroups; ++gi) {
+      if (!groups[gi].u64) continue;
+      const long long cnt = (long long)groups[gi].nsys * grid_n(groups[gi].grid);
+      if (P.ir)
+        WRI_CK(cudaMemcpyAsync(groups[gi].u64, ws + P.v_x64[gi], 16 * (size_t)cnt, cudaMemcpyDeviceToDevice, st));
+      else
+        WRI_CK(launch_widen(groups[gi].u, groups[gi].u64, cnt, st));
+    }
   return WRI_OK;
 }
 
@@ -933,6 +978,9 @@ int wri_source_estimate(const wri_group* groups, int ngroups, int dtype, double*
   int rc = validate_groups(groups, ngroups, false);
   if (rc != WRI_OK) return rc;
   if (!alpha_out) return WRI_EINVAL;
+  bool wide = false;
+  rc = aux_precision(groups, ngroups, dtype, &wide);
+  if (rc != WRI_OK) return rc;
   Plan P;
   plan_aux(groups, ngroups, P);
   rc = check_ws(P, workspace, ws_bytes);
@@ -941,8 +989,8 @@ int wri_source_estimate(const wri_group* groups, int ngroups, int dtype, double*
   char* ws = (char*)workspace;
   rc = upload(groups, ngroups, P, ws, st);
   if (rc != WRI_OK) return rc;
-  Batch b = aux_batch(groups, ngroups, P, ws, dtype);
-  WRI_CK(launch_source_estimate(dtype == WRI_C128 ? 8 : 4, b, P.nsys_total, alpha_out, st));
+  Batch b = aux_batch(groups, ngroups, P, ws, dtype, wide);
+  WRI_CK(launch_source_estimate((dtype == WRI_C128 || wide) ? 8 : 4, b, P.nsys_total, alpha_out, st));
   return WRI_OK;
 }
 
@@ -954,6 +1002,9 @@ int wri_gradient(const wri_group* groups, int ngroups, int dtype, const double* 
   if (!alpha_in || !grad || !f) return WRI_EINVAL;
   for (int gi = 0; gi < ngroups; ++gi)
     if (!grad[gi]) return WRI_EINVAL;
+  bool wide = false;
+  rc = aux_precision(groups, ngroups, dtype, &wide);
+  if (rc != WRI_OK) return rc;
   Plan P;
   plan_aux(groups, ngroups, P);
   rc = check_ws(P, workspace, ws_bytes);
@@ -962,15 +1013,94 @@ int wri_gradient(const wri_group* groups, int ngroups, int dtype, const double* 
   char* ws = (char*)workspace;
   rc = upload(groups, ngroups, P, ws, st);
   if (rc != WRI_OK) return rc;
-  Batch b = aux_batch(groups, ngroups, P, ws, dtype);
+  Batch b = aux_batch(groups, ngroups, P, ws, dtype, wide);
   b.f = f;
   for (int gi = 0; gi < ngroups; ++gi) {
     b.g[gi].alpha = alpha_in + 2 * b.g[gi].sys0;
     b.g[gi].grad = grad[gi];
   }
-  const int rb = dtype == WRI_C128 ? 8 : 4;
+  const int rb = (dtype == WRI_C128 || wide) ? 8 : 4;
   WRI_CK(march(rb, rb, M_GRAD, false, 8, b, st));
-  WRI_CK(launch_data_term(rb, b, P.nsys_total, st));
+  WRI_CK(launch_data_term(rb, dtype == WRI_C128 ? 8 : 4, b, P.nsys_total, st));
+  return WRI_OK;
+}
+
+int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int trial_iters, void* workspace,
+                 size_t ws_bytes, wri_stream_t stream) {
+  int rc = validate_opts(opts);
+  if (rc != WRI_OK) return rc;
+  rc = validate_groups(groups, ngroups, true);
+  if (rc != WRI_OK) return rc;
+  if (trial_iters < 2) return WRI_EINVAL;
+  if (opts->dtype != WRI_C64 || opts->max_refine > 0 || opts->plain || opts->kernel == 1) return WRI_OK;
+  for (int gi = 0; gi < ngroups; ++gi)
+    if (groups[gi].grid.nx % 4 != 0 || (uintptr_t)groups[gi].u % 16 != 0) return WRI_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WRI_ECUDA;
+  std::vector<long long> key = {dev, ngroups};
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const wri_group& G = groups[gi];
+    key.insert(key.end(), {G.grid.nx, G.grid.ny, G.grid.nz, G.nsys, G.rec_off[G.nsys]});
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (const auto& e : g_tuned)
+      if (e.key == key) {
+        opts->kernel = e.kernel;
+        opts->order = e.order;
+        return WRI_OK;
+      }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  WRI_CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return WRI_ECUDA;
+  }
+  static const int kCfgs[] = {7, 8, 9, 10, 11, 13};
+  static const int kOrders[] = {0, 5, 6};
+  float best = 0.f;
+  int best_kernel = 0, best_order = 0;
+  rc = WRI_OK;
+  for (int cfg : kCfgs) {
+    for (int ord : kOrders) {
+      wri_solve_opts o = *opts;
+      o.kernel = 2 + cfg;
+      o.order = ord;
+      o.tol = 0.0;
+      o.warm_start = 0;
+      o.max_iter = trial_iters;
+      Plan P;
+      plan_solve(groups, ngroups, &o, P);
+      if (P.tma_cfg != cfg || check_ws(P, workspace, ws_bytes) != WRI_OK) continue;
+      char* ws = (char*)workspace;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && rc == WRI_OK; ++rep) {  // the first run captures the graph
+        if (cudaEventRecord(e0, st) != cudaSuccess) rc = WRI_ECUDA;
+        if (rc == WRI_OK) rc = upload(groups, ngroups, P, ws, st);
+        if (rc == WRI_OK) rc = solve_fused(groups, ngroups, &o, P, ws, st);
+        if (rc == WRI_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = WRI_ECUDA;
+        if (rc == WRI_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = WRI_ECUDA;
+        if (rc == WRI_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = WRI_ECUDA;
+      }
+      if (rc != WRI_OK) break;
+      if (best_kernel == 0 || ms < best) {
+        best = ms;
+        best_kernel = o.kernel;
+        best_order = ord;
+      }
+    }
+    if (rc != WRI_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != WRI_OK) return rc;
+  if (best_kernel == 0) return WRI_EWORKSPACE;  // no candidate fits the workspace
+  opts->kernel = best_kernel;
+  opts->order = best_order;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_tuned.push_back({key, best_kernel, best_order});
   return WRI_OK;
 }
 

@@ -149,6 +149,8 @@ struct GroupDev {
   void* r64;                // [nsys][n] double2 refinement master of the residual b1 - Z A x (or null)
   void* q64;                // [nsys][n] double2 true residual b1 - Z A x64 of the outer step (or null)
   const void* gvec;         // [nsys][n] complex64 S^H r64, added to s in phase 2 (or null)
+  const int* rmap;          // [nsys][n] receiver entry of a node (-1: none): the FP64 S^H kernels of
+                            // the refinement add lambda P^T r2 in the stencil pass (or null)
   double* grad;             // [n] gradient accumulator (gradient kernel only)
   const float2* ztab;       // [2][nz][3] z-axis coefficients (s_z, 1/(s_z(k-1/2) h^2), 1/(s_z(k+1/2) h^2)),
                             // [0] for A, [1] conjugated for A^H; FP32, built once per solve

@@ -21,11 +21,13 @@ cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* r
                           cudaStream_t st);
 // FP64 refinement (b: inner complex64 view; u: the caller's wavefields, one per group)
 cudaError_t launch_ir_init(const Batch& b, void* const* u, int warm, cudaStream_t st);
+cudaError_t launch_ir_rmap(const Batch& b, int nsys_total, cudaStream_t st);  // b: outer view, map filled with -1
 cudaError_t launch_ir_forcing(const Batch& b, const void* q2, cudaStream_t st);
 cudaError_t launch_ir_update(const Batch& b, cudaStream_t st);
 cudaError_t launch_ir_final(const Batch& b, void* const* u, cudaStream_t st);
 cudaError_t launch_source_estimate(int rbytes, const Batch& b, int nsys_total, double* alpha_out, cudaStream_t st);
-cudaError_t launch_data_term(int rbytes, const Batch& b, int nsys_total, cudaStream_t st);
+cudaError_t launch_data_term(int rbytes, int dbytes, const Batch& b, int nsys_total, cudaStream_t st);
+cudaError_t launch_widen(const void* u, void* u64, long long count, cudaStream_t st);
 
 // unfused baseline kernels (wri_small.cu); pointers are complex of element size rbytes
 cudaError_t plain_fill(int rbytes, void* r1, void* x, long long n, long long src, double ar, double ai,

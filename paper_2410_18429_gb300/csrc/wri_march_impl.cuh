@@ -55,15 +55,8 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     if (MODE == M_P1) {
       const C pn = ldcg_c((const C*)G.p[cur ^ 1] + node);
       rec += (double)lam * (double)lam * (double)abs2(pn);
-    } else if (MODE == M_SH && sizeof(R) != sizeof(OR) && b.flavor != SH_INIT && b.flavor != SH_REF) {
-      // FP64 stencil rounded to complex64 (the refinement's S^H q and S^H r64): near convergence
-      // A^H F and lambda P^T r2 nearly cancel at a receiver, so they are added in FP64 (the node
-      // value recomputed) before the single rounding
-      OC* S = (OC*)G.s;
-      const C af = stencil_at<R, true>(G, (const C*)G.r1[0] + off, b.rec_idx[k]);
-      const C sn = af + lam * r2[k];
-      S[node] = to_c(sn, OR(0));
-      rec += (double)abs2(sn) - (double)abs2(af);
+    } else if (MODE == M_SH && G.rmap) {
+      // the receiver terms were added in the stencil pass (refinement): nothing left to do
     } else if (MODE == M_SH || MODE == M_P2) {
       OC* S = (OC*)G.s;
       const OC sv = ldcg_c(S + node);
@@ -394,6 +387,13 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
             if (MODE == M_APPLY) {
               ((OC*)G.s)[gnode] = to_c(AF, OR(0));
             } else if (MODE == M_SH) {
+              if (G.rmap) {
+                // FP64 normal residual of the refinement: near convergence A^H F and lambda P^T r2
+                // nearly cancel at a receiver, so they are added here, before the one rounding and
+                // before the norm
+                const int rk = G.rmap[gnode];
+                if (rk >= 0) AF = AF + R(G.lambda) * ((const C*)b.r2)[rk];
+              }
               ((OC*)G.s)[gnode] = to_c(AF, OR(0));
               if (sizeof(R) == 4) accf += (float)abs2(AF);
               else accd += (double)abs2(AF);

@@ -43,6 +43,12 @@ cudaError_t launch_ir_init(const Batch& b, void* const* u, int warm, cudaStream_
   return cudaGetLastError();
 }
 
+cudaError_t launch_ir_rmap(const Batch& b, int nsys_total, cudaStream_t st) {
+  if (nsys_total <= 0) return cudaSuccess;
+  k_ir_rmap<<<nsys_total, 128, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ir_forcing(const Batch& b, const void* q2, cudaStream_t st) {
   k_ir_forcing<<<1024, 256, 0, st>>>(b, (const double2*)q2);
   return cudaGetLastError();
@@ -65,9 +71,17 @@ cudaError_t launch_source_estimate(int rbytes, const Batch& b, int nsys_total, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_data_term(int rbytes, const Batch& b, int nsys_total, cudaStream_t st) {
-  if (rbytes == 4) k_data_term<float><<<nsys_total, 256, 0, st>>>(b, nsys_total);
-  else k_data_term<double><<<nsys_total, 256, 0, st>>>(b, nsys_total);
+cudaError_t launch_data_term(int rbytes, int dbytes, const Batch& b, int nsys_total, cudaStream_t st) {
+  if (rbytes == 4 && dbytes == 4) k_data_term<float, float><<<nsys_total, 256, 0, st>>>(b, nsys_total);
+  else if (rbytes == 8 && dbytes == 4) k_data_term<double, float><<<nsys_total, 256, 0, st>>>(b, nsys_total);
+  else if (rbytes == 8 && dbytes == 8) k_data_term<double, double><<<nsys_total, 256, 0, st>>>(b, nsys_total);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const void* u, void* u64, long long count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_widen<<<grid_for(count, 256), 256, 0, st>>>((const float2*)u, (double2*)u64, count);
   return cudaGetLastError();
 }
 

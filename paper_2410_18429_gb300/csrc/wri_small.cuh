@@ -70,6 +70,17 @@ struct IrU {
 
 __device__ __forceinline__ int nsys_of(const Batch& b) { return b.g[b.ngroups - 1].sys0 + b.g[b.ngroups - 1].nsys; }
 
+// Receiver map of the refinement: rmap[system][node] = receiver entry (the map was filled with
+// -1 before); one block per system.
+__global__ void k_ir_rmap(const __grid_constant__ Batch b) {
+  const int s = blockIdx.x;
+  if (s >= nsys_of(b)) return;
+  const SysDev& sd = b.sys[s];
+  const GroupDev& G = b.g[sd.group];
+  int* rmap = const_cast<int*>(G.rmap) + (long long)sd.local * G.n;
+  for (int k = sd.rec_begin + threadIdx.x; k < sd.rec_end; k += blockDim.x) rmap[b.rec_idx[k]] = k;
+}
+
 // x64 = warm ? u : 0, r64 = 0, x32 = 0 on every node; r2_64 = 0 on every receiver entry.
 __global__ void k_ir_init(const __grid_constant__ Batch b, IrU U, int warm) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -185,8 +196,8 @@ __global__ void k_source_estimate(const __grid_constant__ Batch b, int nsys_tota
   alpha_out[2 * s + 1] = (double)a.y;
 }
 
-// f += 1/2 lambda^2 ||P u - d||^2 for every system (one block per system).
-template <typename R>
+// f += 1/2 lambda^2 ||P u - d||^2 for every system (one block per system); u in R, d in DT.
+template <typename R, typename DT>
 __global__ void k_data_term(const __grid_constant__ Batch b, int nsys_total) {
   __shared__ double red[8];
   const int s = blockIdx.x;
@@ -194,11 +205,11 @@ __global__ void k_data_term(const __grid_constant__ Batch b, int nsys_total) {
   const SysDev& sd = b.sys[s];
   const GroupDev& G = b.g[sd.group];
   const cx<R>* u = (const cx<R>*)G.x + (long long)sd.local * G.n;
-  const cx<R>* d = (const cx<R>*)G.d;
+  const cx<DT>* d = (const cx<DT>*)G.d;
   const int base = b.sys[G.sys0].rec_begin;
   double acc = 0.0;
   for (int k = sd.rec_begin + threadIdx.x; k < sd.rec_end; k += blockDim.x) {
-    const cx<R> r = u[b.rec_idx[k]] - d[k - base];
+    const cx<R> r = u[b.rec_idx[k]] - to_c(d[k - base], R(0));
     acc += (double)abs2(r);
   }
   acc = warp_sum(acc);
@@ -210,6 +221,12 @@ __global__ void k_data_term(const __grid_constant__ Batch b, int nsys_total) {
     t *= 0.5 * G.lambda * G.lambda;
     if (t != 0.0) atomicAdd(b.f, t);
   }
+}
+
+// u64 = u widened to complex128 (the FP64 wavefield output of a complex64 solve without refinement).
+__global__ void k_widen(const float2* u, double2* u64, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x)
+    u64[e] = make_double2(u[e].x, u[e].y);
 }
 
 // ------------------------------------------------------------------ unfused baseline kernels

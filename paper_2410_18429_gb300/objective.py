@@ -6,6 +6,9 @@ the gradient needs no adjoint solve (Eq. VarG2): the forward pass solves every
 (source, frequency) system, estimates its weight and accumulates f and g with the
 gradient kernel; the backward pass returns ``grad_output * g``.
 
+With complex64 stencils and FP64 refinement (``opts.max_refine > 0``) the refined FP64
+wavefields are kept (``u64``) and the estimate and gradient run FP64 stencils on them.
+
 Systems are processed in chunks of at most ``max_resident`` systems per group, so the
 wavefields of one chunk are the only ones held in HBM at any time: when the source batch
 outgrows device memory the wavefields are recomputed chunk by chunk instead of stored.
@@ -48,13 +51,13 @@ def chunks(nsys: int, max_resident: int) -> List[tuple]:
     return [(b, min(b + max_resident, nsys)) for b in range(0, nsys, max_resident)]
 
 
-def _sub(g: wri.GroupSpec, b: int, e: int, m, u) -> wri.GroupSpec:
-    """Systems [b, e) of a group, with the model m and the wavefield buffer u."""
+def _sub(g: wri.GroupSpec, b: int, e: int, m, u, u64=None) -> wri.GroupSpec:
+    """Systems [b, e) of a group, with the model m and the wavefield buffers u (and u64)."""
     off = np.asarray(g.rec_off, dtype=np.int64)
     r0, r1 = int(off[b]), int(off[e])
     alpha = None if g.alpha is None else g.alpha[b:e]
     return replace(g, m=m, src=np.asarray(g.src)[b:e], rec_off=(off[b:e + 1] - r0).astype(np.int32),
-                   rec_idx=np.asarray(g.rec_idx)[r0:r1], d=g.d[r0:r1], u=u, alpha=alpha)
+                   rec_idx=np.asarray(g.rec_idx)[r0:r1], d=g.d[r0:r1], u=u, alpha=alpha, u64=u64)
 
 
 def _evaluate(m: torch.Tensor, prob: Problem, want_grad: bool):
@@ -71,11 +74,14 @@ def _evaluate(m: torch.Tensor, prob: Problem, want_grad: bool):
     if tuple(mm.shape) != (prob.groups[0].nz, prob.groups[0].ny, prob.groups[0].nx):
         raise ValueError("the model must have the shape [nz, ny, nx] of the groups' grid")
     iters, status, relres = [], [], []
+    # complex64 with FP64 refinement: the FP64 solution feeds the estimate and the gradient
+    wide = dtype == wri.C64 and int(opts.max_refine) > 0
     for grp in prob.groups:
         step = min(prob.max_resident, grp.nsys)
         u = torch.zeros(step, grp.n, dtype=cdt, device=dev)
+        u64 = torch.zeros(step, grp.n, dtype=torch.complex128, device=dev) if wide else None
         for b, e in chunks(grp.nsys, prob.max_resident):
-            spec = _sub(grp, b, e, mm, u[:e - b])
+            spec = _sub(grp, b, e, mm, u[:e - b], None if u64 is None else u64[:e - b])
             spec.u.zero_()
             it, rr, st = wri.solve([spec], opts)
             if bool((st == wri.SYS_NONFINITE).any()):

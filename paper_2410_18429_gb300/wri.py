@@ -31,7 +31,7 @@ class WriGrid(C.Structure):
 class WriGroup(C.Structure):
     _fields_ = [("grid", WriGrid), ("m", C.c_void_p), ("nsys", C.c_int32), ("src_idx", C.c_void_p),
                 ("rec_off", C.c_void_p), ("rec_idx", C.c_void_p), ("d", C.c_void_p), ("alpha", C.c_void_p),
-                ("lam", C.c_double), ("u", C.c_void_p)]
+                ("lam", C.c_double), ("u", C.c_void_p), ("u64", C.c_void_p)]
 
 
 class WriSolveOpts(C.Structure):
@@ -63,13 +63,14 @@ def _load():
     lib.wri_source_estimate.argtypes = [C.POINTER(WriGroup), i32, i32, dp, vp, sz, vp]
     lib.wri_gradient.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp, sz, vp]
     lib.wri_gradient_noalloc.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp]
+    lib.wri_autotune.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), i32, vp, sz, vp]
     lib.wri_tile_count.argtypes = []
     lib.wri_tile_shape.argtypes = [i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.wri_strerror.argtypes = [i32]
     lib.wri_strerror.restype = C.c_char_p
     lib.wri_version.restype = C.c_char_p
     for f in ("wri_apply_A", "wri_apply_AH", "wri_solve_batch", "wri_source_estimate", "wri_gradient",
-              "wri_gradient_noalloc", "wri_tile_count", "wri_tile_shape"):
+              "wri_gradient_noalloc", "wri_autotune", "wri_tile_count", "wri_tile_shape"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -77,8 +78,8 @@ def _load():
 lib = _load()
 
 EXPORTS = ("wri_apply_A", "wri_apply_AH", "wri_workspace_size", "wri_aux_workspace_size", "wri_solve_batch",
-           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_tile_count", "wri_tile_shape",
-           "wri_strerror", "wri_version")
+           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_autotune", "wri_tile_count",
+           "wri_tile_shape", "wri_strerror", "wri_version")
 
 
 def strerror(code: int) -> str:
@@ -112,6 +113,8 @@ class GroupSpec:
     src: int64 [nsys]; rec_off: int32 [nsys+1]; rec_idx: int32 [nnz] (host numpy);
     d: complex CUDA tensor [nnz]; alpha: float64 CUDA tensor [nsys, 2] or None (source-free);
     u: complex CUDA tensor [nsys, n] (initial guess with warm_start, result on return).
+    u64: optional complex128 CUDA tensor [nsys, n] for complex64 problems: the solve also writes
+    the FP64 solution there, and the source estimate and gradient then read it (FP64 stencils).
     """
 
     nx: int
@@ -130,6 +133,7 @@ class GroupSpec:
     u: object
     alpha: object = None
     pml_R: float = 1e-3
+    u64: object = None
 
     @property
     def n(self) -> int:
@@ -157,7 +161,7 @@ class _Marshal:
                 rec = np.zeros(1, dtype=np.int32)
             self.keep += [src, off, rec]
             arr[i] = WriGroup(g.grid(), _ptr(g.m), len(src), src.ctypes.data, off.ctypes.data, rec.ctypes.data,
-                              _ptr(g.d), _ptr(g.alpha), float(g.lam), _ptr(g.u))
+                              _ptr(g.d), _ptr(g.alpha), float(g.lam), _ptr(g.u), _ptr(g.u64))
         self.arr = arr
         self.n = len(groups)
 
@@ -268,6 +272,22 @@ def gradient_noalloc(groups: Sequence[GroupSpec], dtype: int, alpha, grads, f, s
     _check(lib.wri_gradient_noalloc(m.arr, m.n, dtype, _ptr(a), gp, _ptr(f), _stream(stream)),
            "wri_gradient_noalloc")
     return grads, f
+
+
+def autotune(groups: Sequence[GroupSpec], opts: WriSolveOpts, trial_iters: int = 12, workspace=None, stream=None):
+    """wri_autotune: a copy of opts with the fastest (kernel, order) for this batch.
+
+    The groups' wavefields are overwritten by the trial solves (unless the choice is cached)."""
+    m = _Marshal(groups)
+    dev = groups[0].u.device
+    nbytes = lib.wri_workspace_size(m.arr, m.n, C.byref(opts))
+    if nbytes == 0:
+        raise WriError(EINVAL, "wri_workspace_size")
+    ws = _workspace(nbytes, dev, workspace)
+    out = WriSolveOpts.from_buffer_copy(opts)
+    _check(lib.wri_autotune(m.arr, m.n, C.byref(out), int(trial_iters), _ptr(ws), ws.numel(), _stream(stream)),
+           "wri_autotune")
+    return out
 
 
 def tile_shapes():

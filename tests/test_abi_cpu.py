@@ -111,3 +111,35 @@ def test_apply_rejects_overlap_and_bad_grid(W):
     g2 = W.WriGrid(20, 18, 16, 3, 10.0, 60.0, 2.0, 2000.0)   # pml_R outside (0, 1)
     assert W.lib.wri_apply_A(C.byref(g2), 0, 0x1000, 1, 0x100000, 0x900000, None) == W.EINVAL
     assert W.lib.wri_apply_AH(C.byref(g), 5, 0x1000, 1, 0x100000, 0x900000, None) == W.EINVAL
+
+
+def test_autotune_validates_and_skips_unsupported_batches(W):
+    """Argument errors come back before any device work; batches the TMA phases cannot take
+    (complex128, refinement, the baseline path) return unchanged without touching the device."""
+    m = W._Marshal([_spec(W)])
+    o = W.make_opts()
+    assert W.lib.wri_autotune(m.arr, m.n, C.byref(o), 1, 0x1000, 1 << 30, None) == W.EINVAL
+    assert W.lib.wri_autotune(m.arr, m.n, None, 8, 0x1000, 1 << 30, None) == W.EINVAL
+    bad = W._Marshal([_spec(W, nx=2)])
+    assert W.lib.wri_autotune(bad.arr, bad.n, C.byref(o), 8, 0x1000, 1 << 30, None) == W.EINVAL
+    for kw in (dict(dtype=W.C128), dict(max_refine=2), dict(plain=True), dict(kernel=W.KERNEL_MARCH)):
+        o2 = W.make_opts(**kw)
+        before = bytes(o2)
+        assert W.lib.wri_autotune(m.arr, m.n, C.byref(o2), 8, 0x1000, 1 << 30, None) == W.OK
+        assert bytes(o2) == before
+
+
+def test_fp64_wavefield_must_be_on_every_group_and_aligned(W):
+    """u64 on some groups only, or misaligned, is rejected before any device work."""
+    g1, g2 = _spec(W), _spec(W)
+    g2.u64 = _FakeTensor(0x20000)
+    m = W._Marshal([g1, g2])
+    gp = (C.c_void_p * 2)(0x4000, 0x5000)
+    assert W.lib.wri_gradient(m.arr, 2, W.C64, 0x3000, gp, 0x6000, 0x1000, 1 << 30, None) == W.EINVAL
+    assert W.lib.wri_source_estimate(m.arr, 2, W.C64, 0x3000, 0x1000, 1 << 30, None) == W.EINVAL
+    assert W.lib.wri_gradient_noalloc(m.arr, 2, W.C64, 0x3000, gp, 0x6000, None) == W.EINVAL
+    g1.u64 = _FakeTensor(0x20008)  # both set, one not 16-byte aligned
+    m = W._Marshal([g1, g2])
+    assert W.lib.wri_source_estimate(m.arr, 2, W.C64, 0x3000, 0x1000, 1 << 30, None) == W.EINVAL
+    o = W.make_opts()
+    assert W.lib.wri_solve_batch(m.arr, 2, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 40, None) == W.EINVAL

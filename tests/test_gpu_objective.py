@@ -110,3 +110,41 @@ def test_chunked_and_recomputed_evaluations_agree(W):
     for f, g in res[1:]:
         assert abs(f - res[0][0]) <= 1e-12 * abs(res[0][0])
         assert rel(g, res[0][1]) < 1e-12
+
+
+def _smooth_direction(shape, seed, sigma=2.0):
+    """Unit-norm Gaussian perturbation smoothed over about sigma cells (seeded)."""
+    from scipy.ndimage import gaussian_filter
+    r = synth.rng(seed)
+    v = gaussian_filter(r.standard_normal(shape), sigma)
+    return v / np.linalg.norm(v)
+
+
+def test_mixed_precision_objective_fd_and_oracle_with_recompute(W):
+    """The differentiation pattern at reduced size: complex64 stencils with FP64 refinement,
+    two systems resident at a time, wavefields recomputed in the backward pass.  The gradient
+    matches central differences of f on smooth random perturbations (eps = 1e-3 relative)
+    and the FP64 oracle's gradient to 1e-4."""
+    wri, obj = W
+    G = case(nphys=(18, 16, 14), npml=4, nsys=4, freq=10.0, nrec=9)
+    m32, d32, _ = seen(G, True)
+    groups = _groups(W, G, 0)
+    opts = wri.make_opts(tol=1e-3, max_iter=400000, dtype=0, max_refine=20, refine_tol=1e-9, inner_tol=1e-2)
+    m = _m(G, 0).double().requires_grad_(True)
+    f = obj.objective(m, groups, opts, max_resident=2, recompute=True)
+    f.backward()
+    g = m.grad.clone()
+    _, _, f_ex, g_ex = O.evaluate(G.spec.shape, G.spec.h, G.omega, m32, G.spec.npml, G.v_max, G.src, G.rec_off,
+                                  G.rec_idx, d32, G.lam)
+    assert abs(f.item() - f_ex) <= 1e-6 * abs(f_ex)
+    assert rel(g.cpu().numpy().ravel(), g_ex) < 1e-4
+    mm = m.detach()
+    for k in range(3):
+        dm = torch.as_tensor(_smooth_direction(G.spec.shape, 30 + k)).cuda()
+        eps = 1e-3 * float(mm.norm())
+        with torch.no_grad():
+            fp = obj.objective(mm + eps * dm, groups, opts, max_resident=2).item()
+            fm = obj.objective(mm - eps * dm, groups, opts, max_resident=2).item()
+        fd = (fp - fm) / (2 * eps)
+        an = float((g * dm).sum())
+        assert abs(fd - an) <= 1e-3 * abs(an) + 1e-6 * abs(f_ex) / eps, (k, fd, an)

@@ -252,14 +252,16 @@ def test_pipeline_gradient_matches_oracle(W):
     G = case(nphys=(17, 12, 9), npml=3, nsys=3, freq=14.0)
     m, d, _ = seen(G, True)
     spec = _spec(W, G, 0)
+    spec.u64 = torch.zeros(G.nsys, G.spec.n, dtype=torch.complex128, device="cuda")
     it, rr, st = W.solve([spec], W.make_opts(tol=1e-3, max_iter=200000, dtype=0, max_refine=12,
                                              refine_tol=1e-10, inner_tol=1e-3))
     assert st.cpu().tolist() == [W.SYS_OK] * 3
+    assert rel(spec.u.cpu().numpy(), spec.u64.cpu().numpy()) < 1e-7   # u is the rounded u64
     a = W.source_estimate([spec], 0)
     g, f = W.gradient([spec], 0, a)
     u_ex, a_ex, f_ex, g_ex = O.evaluate(G.spec.shape, G.spec.h, G.omega, m, G.spec.npml, G.v_max, G.src,
                                         G.rec_off, G.rec_idx, d, G.lam)
-    assert rel(spec.u.cpu().numpy(), u_ex) < 1e-5
+    assert rel(spec.u64.cpu().numpy(), u_ex) < 1e-5
     assert rel(a.cpu().numpy(), a_ex) < 1e-5
     assert rel(g[0].cpu().numpy().ravel(), g_ex) < 1e-4
     assert abs(f.item() - f_ex) <= 1e-4 * abs(f_ex)
@@ -312,6 +314,28 @@ def test_tma_batch_of_groups_equals_single_systems(W, kernel):
                 W.solve([sp1], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_MARCH))
                 assert rel(got[i], sp1.u.cpu().numpy()[0]) < 1e-5, (order, i)
                 i += 1
+
+
+def test_autotune_choice_solves_like_default_and_is_cached(W):
+    """wri_autotune picks a TMA configuration and order; solving with it gives the iterates of
+    the default configuration, and a second call for the same batch shape is served from the
+    cache without touching the wavefields."""
+    G1 = case(nphys=(28, 12, 10), npml=4, nsys=3, seed=5)
+    G2 = case(nphys=(16, 19, 8), npml=4, nsys=2, seed=8, freq=9.0)
+    s1, s2 = _spec(W, G1, 0), _spec(W, G2, 0)
+    base = W.make_opts(tol=0.0, max_iter=20, dtype=0)
+    tuned = W.autotune([s1, s2], base, trial_iters=6)
+    assert 2 + 7 <= tuned.kernel <= 2 + 13 and tuned.order in (0, 5, 6)
+    s1.u.fill_(3.0)
+    again = W.autotune([s1, s2], base, trial_iters=6)
+    assert (again.kernel, again.order) == (tuned.kernel, tuned.order)
+    assert float(s1.u.real.min()) == 3.0 == float(s1.u.real.max())
+    a1, a2 = _spec(W, G1, 0), _spec(W, G2, 0)
+    W.solve([a1, a2], tuned)
+    b1, b2 = _spec(W, G1, 0), _spec(W, G2, 0)
+    W.solve([b1, b2], base)
+    assert rel(a1.u.cpu().numpy(), b1.u.cpu().numpy()) < 1e-5
+    assert rel(a2.u.cpu().numpy(), b2.u.cpu().numpy()) < 1e-5
 
 
 def test_plain_path_matches_fused(W):
