@@ -364,7 +364,17 @@ def main():
         at_tol["value"] = nsys / t_eq
         extras["at_tolerance"] = at_tol
 
-        # ---- end to end through the public API with host buffers
+        if ws == 1:
+            samples = 4
+            val, rate, secs, busy = cpu_rate(groups, iters_done, args.cpu_iters * 2, samples, 1)
+            extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": max(1, round(busy)), "kind": "oracle",
+                                      "sample": cpu_sample_text(groups, args.cpu_iters * 2, samples),
+                                      "gpt_iter_s": rate / 1e9, "seconds_sampled": secs, "busy_threads": busy,
+                                      "host_threads": len(os.sched_getaffinity(0))}
+
+    # ---- end to end through the public API with host buffers, on every rank (the gradient sum
+    # over ranks included), timed like the device-resident steps (barrier, max over ranks)
+    if not args.no_extras:
         m_host = [torch.from_numpy(np.ascontiguousarray(g.m, dtype=np.float32).reshape(g.spec.shape)).pin_memory()
                   for g in groups]
         d_host = [torch.from_numpy(np.ascontiguousarray(g.d, dtype=np.complex64)).pin_memory() for g in groups]
@@ -375,15 +385,17 @@ def main():
         d2h = sum(x.numel() * x.element_size() for x in g_host) + 8 + a_host.numel() * 16
 
         def e2e_step():
-            for s, mh, dh in zip(specs, m_host, d_host):
-                s.m.copy_(mh, non_blocking=True)
-                s.d.copy_(dh, non_blocking=True)
+            for s_, mh, dh in zip(specs, m_host, d_host):
+                s_.m.copy_(mh, non_blocking=True)
+                s_.d.copy_(dh, non_blocking=True)
             wri.solve(specs, opts, workspace=work)
             a = wri.source_estimate(specs, wri.C64, workspace=work)
             for g in grads:
                 g.zero_()
             f.zero_()
             wri.gradient(specs, wri.C64, a, grads=grads, f=f, workspace=work)
+            if ws > 1:
+                allreduce_gradient(grads, f)
             for gh, g in zip(g_host, grads):
                 gh.copy_(g, non_blocking=True)
             f_host.copy_(f, non_blocking=True)
@@ -391,6 +403,7 @@ def main():
 
         e2e_step()
         torch.cuda.synchronize()
+        barrier()
         c0, c1 = ev(), ev()
         ne = max(2, args.steps // 2)
         c0.record(stream)
@@ -398,16 +411,15 @@ def main():
             e2e_step()
         c1.record(stream)
         torch.cuda.synchronize()
+        barrier()
         te = c0.elapsed_time(c1) / 1e3
-        extras["e2e"] = {"value": nsys * ne / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        if ws > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([te], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        extras["e2e"] = {"value": ws * nsys * ne / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h}
-        if ws == 1:
-            samples = 4
-            val, rate, secs, busy = cpu_rate(groups, iters_done, args.cpu_iters * 2, samples, 1)
-            extras["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": max(1, round(busy)), "kind": "oracle",
-                                      "sample": cpu_sample_text(groups, args.cpu_iters * 2, samples),
-                                      "gpt_iter_s": rate / 1e9, "seconds_sampled": secs, "busy_threads": busy,
-                                      "host_threads": len(os.sched_getaffinity(0))}
 
     # kernels of libwri per step: set-up of the right-hand sides, z tables, initial S^H b, 2 phase kernels
     # per CG iteration in graph replays of K_POLL iterations (the last replay holds the x-only pass),

@@ -118,7 +118,7 @@ typedef struct {
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
   int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
-                          1 = z-march kernels only, 2 + c = TMA configuration c (0..13; 9..13
+                          1 = z-march kernels only, 2 + c = TMA configuration c (0..16; 9..16
                           are the warp-specialised kernels); see wri_autotune */
   int32_t order;       /* TMA phases: 0 = automatic, 1 = tiles of a system consecutive,
                           2 = systems of a tile consecutive, 3 = z-chunk slowest,
@@ -208,14 +208,17 @@ WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype
 WRI_API int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int trial_iters,
                          void* workspace, size_t ws_bytes, wri_stream_t stream);
 
-/* Number of built tile configurations and the thread-block shape of one of them. */
+/* Number of built tile configurations of the z-march kernels and the thread-block shape of one
+ * of them (tile = 1..count; WRI_EINVAL otherwise).  Outside the paper: an implementation
+ * choice exposed for tuning. */
 WRI_API int wri_tile_count(void);
 WRI_API int wri_tile_shape(int tile, int* bx, int* by);
 
-/* Static description of an error code. */
+/* Static description of an error code (never NULL; "unknown error code" for other values). */
 WRI_API const char* wri_strerror(int code);
 
-/* Library version string. */
+/* Library version string, with the hash of the kernel sources it was built from (profiles
+ * record it, so measurements taken on another build can be told apart). */
 WRI_API const char* wri_version(void);
 
 #ifdef __cplusplus

@@ -27,6 +27,7 @@ constexpr int kRefSMs = 152;  // SMs of a GB300; sets the z-split of small batch
 // system run together, so their halos meet in L2); L2 fills of 64 bytes on a copy miss
 // (128-byte fills over-fetch the halo columns).  wri_autotune refines the choice per batch.
 constexpr int kDefaultTmaCfg = 9;
+constexpr int kFirstWsCfg = 9;  // configurations from here on are the warp-specialised kernels
 constexpr int kDefaultOrder = 6;
 constexpr int kDefaultPromotion = 2;
 constexpr size_t kAlign = 256;
@@ -183,12 +184,15 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
   P.ir = (o->dtype == WRI_C64 && o->max_refine > 0) ? 1 : 0;
   P.by = by_of_tile(o->tile);
   P.tma_cfg = -1;
-  if (!o->plain && o->kernel != 1 && o->dtype == WRI_C64 && !P.ir) {
+  if (!o->plain && o->kernel != 1 && o->dtype == WRI_C64) {
     bool ok = true;
+    // the refinement's inner iterate lives in the workspace; otherwise the TMA phases update u
     for (int gi = 0; gi < ngroups; ++gi)
-      ok = ok && (groups[gi].grid.nx % 4 == 0) && ((uintptr_t)groups[gi].u % 16 == 0);
+      ok = ok && (groups[gi].grid.nx % 4 == 0) && (P.ir || (uintptr_t)groups[gi].u % 16 == 0);
     if (ok) {
       P.tma_cfg = o->kernel >= 2 ? o->kernel - 2 : kDefaultTmaCfg;
+      // the refinement's inner phase 2 adds S^H r64, which only the warp-specialised kernels do
+      if (P.ir && P.tma_cfg < kFirstWsCfg) P.tma_cfg = kDefaultTmaCfg;
       P.by = tma_config_by(P.tma_cfg);
     }
   }
@@ -620,6 +624,17 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
     gb.g[gi].s = const_cast<void*>(inner.g[gi].gvec);
   }
   const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
+  // inner solves on the warp-specialised TMA phases when the batch allows them
+  const TmaSet* tma = nullptr;
+  static thread_local TmaSet T;
+  if (P.tma_cfg >= 0) {
+    const int ord = o->order ? o->order : kDefaultOrder;
+    inner.order = (ord == 1) ? 1 : (ord == 3) ? 2 : (ord >= 4) ? 3 : 0;
+    inner.sblock = (ord >= 4) ? (1 << (ord - 2)) : 1;
+    WRI_CK(launch_ztable(inner, st));
+    if (build_tma(inner, P, inner.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, T))
+      tma = &T;
+  }
   for (int outer_k = 0;; ++outer_k) {
     WRI_CK(cudaMemsetAsync(outer.remaining, 0, 2 * sizeof(int), st));
     Batch r = outer;
@@ -632,7 +647,7 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
     WRI_CK(cudaStreamSynchronize(st));
     if (*c->pinned <= 0) break;
     WRI_CK(launch_march_f64_to_f32(M_SH, P.by, gb, 0, st));        // g' = S^H r64
-    const int rc = run_loop(P, inner, inner, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st);
+    const int rc = run_loop(P, inner, inner, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, tma);
     if (rc != WRI_OK) return rc;
     WRI_CK(launch_ir_update(inner, st));                           // x64 += dx, r64 += dr
     if (outer_k > o->max_refine + 1) return WRI_ECUDA;
@@ -1058,7 +1073,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
     cudaEventDestroy(e0);
     return WRI_ECUDA;
   }
-  static const int kCfgs[] = {7, 8, 9, 10, 11, 13};
+  static const int kCfgs[] = {8, 9, 11, 12, 13, 14};
   static const int kOrders[] = {0, 5, 6};
   float best = 0.f;
   int best_kernel = 0, best_order = 0;

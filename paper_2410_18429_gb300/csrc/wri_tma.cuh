@@ -12,8 +12,8 @@
 //     independently of its registers and warps.
 // The consumers form F = a + c b on the halo'd tile into a ring of 4 F planes (own
 // nodes stored as the updated CG vector), then apply the stencil one plane behind.
-// Every mbarrier wait is bounded: on time-out the CTA records an error flag, drains
-// its own copies (again bounded) and stops.
+// Every mbarrier wait is bounded (2 s of the global timer): on time-out the CTA records an error
+// flag, drains its own copies (again bounded) and stops.
 #pragma once
 
 #include <cuda.h>
@@ -50,10 +50,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: false after ~2^24 polls (seconds), which only a broken copy can cause
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Time limit of every wait of the copy pipelines: only a copy that never completes (a broken
+// descriptor or protocol) can reach it.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// bounded wait: false after 2 s of polling (or 2^26 polls, whichever comes first)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 24); ++i)
+  const uint64_t t0 = global_ns();
+  for (int i = 0; i < (1 << 26); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
   return false;
 }
 
@@ -709,9 +722,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // bounded wait that also gives up as soon as another role raised the abort flag
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
-  for (int i = 0; i < (1 << 24); ++i) {
+  const uint64_t t0 = global_ns();
+  for (int i = 0; i < (1 << 26); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 63 && *abort_flag) return false;
+    if ((i & 63) == 63 && (*abort_flag || global_ns() - t0 > kWaitLimitNs)) return false;
   }
   return false;
 }
@@ -733,9 +747,14 @@ __device__ __forceinline__ float2 fma_c(float c, float2 b, float2 a) {
   return make_float2(__fmaf_rn(c, b.x, a.x), __fmaf_rn(c, b.y, a.y));
 }
 
-template <int MODE, int BY, int S, int MINB>
-__global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_constant__ Batch b,
-                                                                  const __grid_constant__ TmaSet T) {
+// PW = true: a dedicated copy warp (16 BY + 32 threads).  PW = false: no copy warp (16 BY threads,
+// so more CTAs fit the register file); thread 0 issues the copies of its CTA's planes itself,
+// S - 2 planes ahead of the plane it consumes, each after that stage's "empty" barrier (the
+// stage of two planes back, which every warp has released by then); copies never run ahead
+// across a work item.
+template <int MODE, int BY, int S, int MINB, bool PW = true>
+__global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(const __grid_constant__ Batch b,
+                                                                             const __grid_constant__ TmaSet T) {
   static_assert(MODE == M_P1 || MODE == M_P2, "the warp-specialised path covers the two CGLS phases");
   static_assert(S >= 3, "two stages are held by the consumers");
   typedef float2 C;
@@ -770,7 +789,7 @@ __global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_co
   __syncthreads();  // the only CTA-wide barrier: the copy warp leaves the consumers' barriers after it
 
   // ================================================================ copy warp
-  if (tid >= NC) {
+  if (PW && tid >= NC) {
     if (tid != NC) return;
     unsigned fills = 0;
     bool stop = false;
@@ -832,6 +851,7 @@ __global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_co
   const int o = (ty + 1) * L::HW + 2 * tx + 2;  // own pair in a halo box
   const int oc = ty * WRI_TX + 2 * tx;          // own pair in a 32 x BY box
   unsigned fills = 0;
+  unsigned issued = 0;  // PW = false: copies issued by thread 0
 
   for (long long item = blockIdx.x; item < b.nitems; item += gridDim.x) {
     const int gi = find_group(b, item);
@@ -886,6 +906,30 @@ __global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_co
       }
       const int src_lane = (src_col == col) ? 0 : (src_col == col + 1) ? 1 : -1;
       const int count = z1 - z0 + 2;
+      // PW = false: thread 0 issues fill q of this item (plane z0 - 1 + q) into stage (fills + q) % S
+      auto fill = [&](int q) {
+        const unsigned u = fills + (unsigned)q;
+        const int st = (int)(u % S);
+        if (u >= (unsigned)S && !mbar_wait_or_abort(&empty[st], ((u / S) - 1) & 1u, &s_abort)) {
+          s_abort = 1;
+          atomicExch(T.err, 1);
+          return;
+        }
+        if (s_abort) return;
+        const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
+        const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
+        const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + L::MB;
+        unsigned char* base = smem + (size_t)st * L::STAGE;
+        const int kq = z0 - 1 + q;
+        mbar_expect_tx(&full[st], tx_bytes);
+        tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
+        if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &full[st]);
+        if (hasX) tma_load_4d(base + L::OFF_X, &T.map[gi][TM_X], x0, y0, kq, sl, &full[st]);
+        tma_load_3d(base + L::OFF_M, &T.map[gi][TM_M], x0, y0, kq, &full[st]);
+        issued = u + 1;
+      };
+      if (!PW && tid == 0)
+        for (int q = 0; q < S - 2 && q < count; ++q) fill(q);
 
       int xlo, xhi, ylo, yhi, zlo, zhi;
       interior_range(G.ax, xlo, xhi);
@@ -915,7 +959,8 @@ __global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_co
       const float ih2 = G.ih2f;
       const float2* ztab = G.ztab + (CONJ ? 3 * nz : 0);
 
-      CompSum acc;
+      // per-thread partial sum: FP32 over 4 planes (8 terms), then FP64
+      float accf = 0.f;
       C fm0 = czero<float>(), fm1 = fm0, fc0 = fm0, fc1 = fm0;  // own F of planes kq-2, kq-1
       float2 m_c = make_float2(0.f, 0.f);                        // m of plane kq-1
       long long po = (long long)(z0 - 1) * plane;
@@ -1029,16 +1074,20 @@ __global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_co
                 a1 = a1 + hi2(gv);
               }
               st4(pO + po - plane, a0, a1);
-              acc.add(abs2(a0));
-              acc.add(abs2(a1));
+              accf += abs2(a0) + abs2(a1);
             }
           }
+        }
+        if ((q & 3) == 3) {
+          accd += (double)accf;
+          accf = 0.f;
         }
         if (q >= 1) {
           // plane kq-1 is done: hand its stage back to the copy warp
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[(u - 1) % S]);
         }
+        if (!PW && tid == 0 && q + S - 2 < count) fill(q + S - 2);
         fm0 = fc0;
         fm1 = fc1;
         fc0 = v0;
@@ -1048,7 +1097,7 @@ __global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_co
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[(fills + count - 1) % S]);
       fills += (unsigned)count;
-      accd = acc.value();
+      accd += (double)accf;
     }
 
     // ---- tile partial, ticket and the system's finalizer (consumer threads only)
@@ -1064,6 +1113,11 @@ __global__ void __launch_bounds__(16 * BY + 32, MINB) k_phase_ws(const __grid_co
     }
     CSync::sync();
     if (s_last) finalize<float, float, MODE, NC, CSync>(b, G, sd, sl, xonly, red, &bcast);
+  }
+  if (!PW && tid == 0 && s_abort) {
+    // stopped early: wait (bounded) until every copy thread 0 issued has landed
+    const unsigned first = issued > (unsigned)S ? issued - S : 0u;
+    for (unsigned u = first; u < issued; ++u) mbar_wait(&full[u % S], (u / S) & 1u);
   }
 }
 

@@ -88,17 +88,17 @@ def test_fixed_iterations_match_oracle_cgls(W, dtype, tol, source_free):
         assert abs(rr.cpu().numpy()[s] - rr_k) <= max(tol, 1e-6) * rr_k * 10
 
 
-@pytest.mark.parametrize("cfg", list(range(14)))
+@pytest.mark.parametrize("cfg", list(range(17)))
 @pytest.mark.parametrize("source_free", [True, False])
 def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
-    """TMA-pipelined phases (x extent a multiple of 4; configurations 9-13 are the
+    """TMA-pipelined phases (x extent a multiple of 4; configurations 9-16 are the
     warp-specialised kernels): ragged 32 x BY tiles, iterates of k CGLS steps equal the
     oracle's and the z-march kernels' (same tile height)."""
     G = case(nphys=(36, 13, 10), npml=4, nsys=3)
     m, d, al = seen(G, True)
     A = oracle_A(G, m)
     k = 25
-    by = 16 if cfg in (2, 3, 4, 5, 12) else 8
+    by = 16 if cfg in (2, 3, 4, 5, 12, 16) else 8
     s_t, s_m = _spec(W, G, 0, source_free), _spec(W, G, 0, source_free)
     it_t, rr_t, st_t = W.solve([s_t], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_TMA(cfg)))
     it_m, rr_m, st_m = W.solve([s_m], W.make_opts(tol=0.0, max_iter=k, dtype=0, kernel=W.KERNEL_MARCH,
@@ -114,7 +114,7 @@ def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
         assert rel(u_t[s], x_k) < 3e-4
 
 
-@pytest.mark.parametrize("cfg", [0, 8, 9])
+@pytest.mark.parametrize("cfg", [0, 8, 9, 14])
 def test_tma_z_chunks_and_convergence(W, cfg):
     """TMA path with z-chunks and a real stopping test: same iterations (within 5 %) and
     wavefields as the z-march kernels at tolerance 1e-3."""
@@ -165,6 +165,28 @@ def test_mixed_precision_refinement_matches_exact(W, source_free):
     u = spec.u.cpu().numpy()
     for s in range(2):
         assert rel(u[s], _exact(G, m, d, source_free, s)) < 1e-5
+
+
+@pytest.mark.parametrize("source_free", [True, False])
+def test_refinement_on_tma_phases_matches_exact(W, source_free):
+    """x extent a multiple of 4 (24): the refinement's inner solves run on the warp-specialised TMA
+    phases (phase 2 adds S^H r64); the FP64 wavefield reaches the exact solution of the float32
+    model / complex64 data problem, and the same refinement on the z-march kernels agrees."""
+    G = case(nphys=(16, 11, 9), npml=4, nsys=2, freq=15.0)
+    m, d, _ = seen(G, True)
+    out = []
+    for kernel in (0, 1):
+        spec = _spec(W, G, 0, source_free)
+        spec.u64 = torch.zeros(G.nsys, G.spec.n, dtype=torch.complex128, device="cuda")
+        it, rr, st = W.solve([spec], W.make_opts(tol=1e-3, max_iter=200000, dtype=0, max_refine=12,
+                                                 refine_tol=1e-10, inner_tol=1e-2, kernel=kernel))
+        assert st.cpu().tolist() == [W.SYS_OK] * 2, (kernel, st, rr, it)
+        assert float(rr.max()) <= 1e-10
+        out.append(spec.u64.cpu().numpy())
+    for s in range(2):
+        ex = _exact(G, m, d, source_free, s)
+        assert rel(out[0][s], ex) < 1e-8
+        assert rel(out[1][s], ex) < 1e-8
 
 
 @pytest.mark.parametrize("k", [5, 25])
@@ -325,7 +347,7 @@ def test_autotune_choice_solves_like_default_and_is_cached(W):
     s1, s2 = _spec(W, G1, 0), _spec(W, G2, 0)
     base = W.make_opts(tol=0.0, max_iter=20, dtype=0)
     tuned = W.autotune([s1, s2], base, trial_iters=6)
-    assert 2 + 7 <= tuned.kernel <= 2 + 13 and tuned.order in (0, 5, 6)
+    assert tuned.kernel in [2 + c for c in (8, 9, 11, 12, 13, 14)] and tuned.order in (0, 5, 6)
     s1.u.fill_(3.0)
     again = W.autotune([s1, s2], base, trial_iters=6)
     assert (again.kernel, again.order) == (tuned.kernel, tuned.order)
@@ -391,6 +413,19 @@ def test_max_iter_one_and_status(W):
         W.solve([spec], W.make_opts(tol=-1.0, dtype=0))
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_nonfinite_model_is_reported_per_group(W, kernel):
+    """A NaN in one group's model: its systems end with WRI_SYS_NONFINITE, the other group's
+    systems converge as usual, and the call returns (TMA phases and z-march kernels)."""
+    G1 = case(nphys=(28, 12, 10), npml=4, nsys=2, seed=5)
+    G2 = case(nphys=(16, 13, 9), npml=4, nsys=3, seed=8, freq=9.0)   # x extents 36 and 24: TMA-eligible
+    s1, s2 = _spec(W, G1, 0), _spec(W, G2, 0)
+    s2.m.view(-1)[s2.m.numel() // 2] = float("nan")
+    it, rr, st = W.solve([s1, s2], W.make_opts(tol=1e-3, max_iter=100000, dtype=0, kernel=kernel))
+    assert st.cpu().tolist() == [W.SYS_OK] * 2 + [W.SYS_NONFINITE] * 3
+    assert float(rr[:2].max()) <= 1e-3
+
+
 @pytest.mark.parametrize("tile", [1, 2, 3])
 def test_tile_shapes_agree(W, tile):
     G = case(nphys=(40, 23, 9), npml=4, nsys=2)
@@ -446,3 +481,65 @@ def test_full_size_batched_iterations_consistent(W):
         sb[rec] = grp.lam ** 2 * d
         true_rr = (sv.norm() / sb.norm()).item()
         assert abs(true_rr - rr[s].item()) <= 2e-3 * true_rr, (true_rr, rr[s].item())
+
+
+def test_config5_scale_refinement_residual(W):
+    """256 x 256 x 160 physical nodes + 10-cell layer (276 x 276 x 180 = 13.7 M nodes), h = 8 m, salt
+    body, 10 Hz, 2 systems, complex64 with FP64 refinement: after one refinement step of 60 inner
+    iterations the reported FP64 residual equals ||S^H (b - S u64)|| / ||S^H b|| recomputed with the
+    complex128 operator kernels (same float32 model and complex64 data), and u is u64 rounded."""
+    grp = synth.workload_c5(nsrc=2)
+    n = grp.spec.n
+    m32 = grp.m.astype(np.float32).astype(np.float64)
+    d32 = grp.d.astype(np.complex64).astype(np.complex128)
+    from paper_2410_18429_gb300.problem import to_device
+    spec = to_device(grp, 0, "cuda")
+    spec.u64 = torch.zeros(2, n, dtype=torch.complex128, device="cuda")
+    it, rr, st = W.solve([spec], W.make_opts(tol=1e-3, max_iter=60, dtype=0, max_refine=1, refine_tol=1e-12,
+                                             inner_tol=1e-12))
+    assert it.cpu().tolist() == [60, 60] and st.cpu().tolist() == [W.SYS_MAXITER] * 2
+    assert rel(spec.u.cpu().numpy(), spec.u64.cpu().numpy()) < 1e-7
+    spec64 = to_device(grp, 1, "cuda", m=m32, d=d32)
+    for s in range(2):
+        us = spec.u64[s:s + 1]
+        Au = W.apply_A(spec64, us)[0]
+        Au[grp.src[s]] = 0
+        rec = torch.as_tensor(grp.rec_idx[grp.rec_off[s]:grp.rec_off[s + 1]].astype(np.int64)).cuda()
+        d = torch.as_tensor(d32[grp.rec_off[s]:grp.rec_off[s + 1]]).cuda()
+        r2 = grp.lam * (d - us[0, rec])
+        sv = W.apply_A(spec64, (-Au)[None], adjoint=True)[0]
+        sv[rec] += grp.lam * r2
+        sb = torch.zeros(n, dtype=torch.complex128, device="cuda")
+        sb[rec] = grp.lam ** 2 * d
+        true_rr = (sv.norm() / sb.norm()).item()
+        assert abs(true_rr - rr[s].item()) <= 1e-6 * true_rr, (true_rr, rr[s].item())
+    del spec, spec64
+    torch.cuda.empty_cache()
+
+
+def test_config2_tolerance_halving_with_warm_starts(W):
+    """Configuration 2's batch shape (64^3 + 10-cell layer, layered model, surface sources x 3 Hz,
+    5 Hz, 7 Hz in one batched complex64 solve; 2 sources per frequency) through the tolerance
+    halving of Algorithm 2 (eps, eps/2, eps/4 from eps = 0.2), each step warm-started from the last:
+    every system meets each tolerance, and the warm-started last step needs fewer iterations than a
+    cold solve to the same tolerance.  (At 50-100 points per wavelength unpreconditioned CGLS needs
+    more than 2e5 iterations to reach 1e-2 on this grid, so the schedule starts looser.)"""
+    from paper_2410_18429_gb300.problem import to_device
+    groups = []
+    for g in synth.workload_c2():
+        groups.append(synth.Group(g.spec, g.freq, g.v, g.src[:2], g.rec_off[:3] - g.rec_off[0],
+                                  g.rec_idx[g.rec_off[0]:g.rec_off[2]], g.lam, g.v_max, g.pml_R, g.alpha[:2],
+                                  g.d[g.rec_off[0]:g.rec_off[2]]))
+    specs = [to_device(g, 0, "cuda") for g in groups]
+    nsys = sum(g.nsys for g in groups)
+    tols = [0.2, 0.1, 0.05]
+    iters = []
+    for k, tol in enumerate(tols):
+        it, rr, st = W.solve(specs, W.make_opts(tol=tol, max_iter=100000, dtype=0, warm_start=k > 0))
+        assert st.cpu().tolist() == [W.SYS_OK] * nsys
+        assert float(rr.max()) <= tol
+        iters.append(it.cpu().numpy())
+    cold = [to_device(g, 0, "cuda") for g in groups]
+    it_cold, rr_cold, st_cold = W.solve(cold, W.make_opts(tol=tols[-1], max_iter=100000, dtype=0))
+    assert st_cold.cpu().tolist() == [W.SYS_OK] * nsys
+    assert np.all(iters[-1] < it_cold.cpu().numpy())
