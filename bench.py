@@ -303,11 +303,14 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / t_iter / 1e9
+    # DRAM traffic per iteration from the ncu record of this build and kernel configuration
     traffic = None
+    cfg = int(opts.kernel) - 2 if int(opts.kernel) >= 2 else None
     try:
         prof = json.load(open(TRAFFIC_FILE))
-        if prof.get("kernel_version") == wri.version():
-            traffic = prof["bytes_per_node_system"] * node_sys
+        rec = prof.get("configs", {}).get(str(cfg))
+        if prof.get("kernel_version") == wri.version() and rec:
+            traffic = rec["bytes_per_node_system"] * node_sys
     except (OSError, KeyError, ValueError):
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

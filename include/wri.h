@@ -118,7 +118,7 @@ typedef struct {
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
   int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
-                          1 = z-march kernels only, 2 + c = TMA configuration c (0..16; 9..16
+                          1 = z-march kernels only, 2 + c = TMA configuration c (0..19; 9..19
                           are the warp-specialised kernels); see wri_autotune */
   int32_t order;       /* TMA phases: 0 = automatic, 1 = tiles of a system consecutive,
                           2 = systems of a tile consecutive, 3 = z-chunk slowest,

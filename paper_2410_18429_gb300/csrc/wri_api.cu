@@ -1073,7 +1073,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
     cudaEventDestroy(e0);
     return WRI_ECUDA;
   }
-  static const int kCfgs[] = {8, 9, 11, 12, 13, 14};
+  static const int kCfgs[] = {8, 9, 12, 13, 17, 18};
   static const int kOrders[] = {0, 5, 6};
   float best = 0.f;
   int best_kernel = 0, best_order = 0;

@@ -58,11 +58,11 @@ static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStr
   return cudaGetLastError();
 }
 
-template <int MODE, int BY, int S, int MINB, bool PW = true>
+template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
 static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   static int occ = -1;
   const size_t smem = WsLayout<MODE, BY>::bytes(S);
-  auto kern = k_phase_ws<MODE, BY, S, MINB, PW>;
+  auto kern = k_phase_ws<MODE, BY, S, MINB, PW, ER>;
   constexpr int threads = 16 * BY + (PW ? 32 : 0);
   if (occ < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -86,14 +86,15 @@ static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStre
   return cudaGetLastError();
 }
 
-int tma_config_count() { return 17; }
+int tma_config_count() { return 20; }
 
 // config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4) with one node per thread;
 // 4 -> (16, 4), 5 -> (16, 3), 6 -> (8, 6), 7 -> (8, 3; 5 CTAs/SM), 8 -> (8, 4; 4 CTAs/SM) with two
 // x-adjacent nodes per thread; warp-specialised (copy warp + consumer warps, two nodes per
 // thread): 9 -> (8, 4 stages; 4 CTAs/SM), 10 -> (8, 4; 5 CTAs/SM), 11 -> (8, 6; 3), 12 -> (16, 4; 2),
 // 13 -> (8, 5; 4); without the copy warp (thread 0 issues the copies): 14 -> (8, 4; 5 CTAs/SM),
-// 15 -> (8, 4; 4), 16 -> (16, 4; 3)
+// 15 -> (8, 4; 4), 16 -> (16, 4; 3); copy warp and early stage release: 17 -> (8, 4; 4),
+// 18 -> (8, 3; 4), 19 -> (8, 5; 4)
 int tma_config_by(int cfg) {
   return (cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5 || cfg == 12 || cfg == 16) ? 16 : 8;
 }
@@ -146,6 +147,15 @@ cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T,
   WRI_WS1_CASE(M_P1, 16, 16, 4, 3)
   WRI_WS1_CASE(M_P2, 16, 16, 4, 3)
 #undef WRI_WS1_CASE
+#define WRI_WSE_CASE(M, C_, BY_, S_, MB_) \
+  if (mode == M && cfg == C_) return launch_ws<M, BY_, S_, MB_, true, true>(b, T, grid, st);
+  WRI_WSE_CASE(M_P1, 17, 8, 4, 4)
+  WRI_WSE_CASE(M_P2, 17, 8, 4, 4)
+  WRI_WSE_CASE(M_P1, 18, 8, 3, 4)
+  WRI_WSE_CASE(M_P2, 18, 8, 3, 4)
+  WRI_WSE_CASE(M_P1, 19, 8, 5, 4)
+  WRI_WSE_CASE(M_P2, 19, 8, 5, 4)
+#undef WRI_WSE_CASE
   return cudaErrorInvalidValue;
 }
 

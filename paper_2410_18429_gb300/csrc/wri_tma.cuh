@@ -752,11 +752,18 @@ __device__ __forceinline__ float2 fma_c(float c, float2 b, float2 a) {
 // S - 2 planes ahead of the plane it consumes, each after that stage's "empty" barrier (the
 // stage of two planes back, which every warp has released by then); copies never run ahead
 // across a work item.
-template <int MODE, int BY, int S, int MINB, bool PW = true>
+//
+// ER = true ("early release"): a stage is used in one pass only.  When plane k arrives a thread
+// forms its own F(k), completes the pending stencil of plane k-1 with it as the z+1 neighbour,
+// and computes everything of plane k's stencil except the z+1 term (A u is linear in it: the
+// partial value and the z+1 coefficient stay in registers), then releases the stage at once:
+// S - 1 planes of copies stay in flight instead of S - 2.
+template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
 __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(const __grid_constant__ Batch b,
                                                                              const __grid_constant__ TmaSet T) {
   static_assert(MODE == M_P1 || MODE == M_P2, "the warp-specialised path covers the two CGLS phases");
   static_assert(S >= 3, "two stages are held by the consumers");
+  static_assert(PW || !ER, "early release is built with the copy warp");
   typedef float2 C;
   typedef WsLayout<MODE, BY> L;
   typedef FirstThreadsSync<16 * BY> CSync;
@@ -961,6 +968,139 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
 
       // per-thread partial sum: FP32 over 4 planes (8 terms), then FP64
       float accf = 0.f;
+      if constexpr (ER) {
+        C fc0 = czero<float>(), fc1 = fc0;                       // own F of plane kq-1
+        C p0 = fc0, p1 = fc0, c0 = fc0, c1 = fc0;               // pending stencil of kq-1 without z+1
+        long long po = (long long)(z0 - 1) * plane;
+        for (int q = 0; q < count; ++q, po += plane) {
+          const unsigned u = fills + q;
+          const int st = (int)(u % S);
+          bool ok = true;
+          if (!s_abort) {
+            ok = mbar_wait_or_abort(&full[st], (u / S) & 1u, &s_abort);
+            if (!ok) {
+              s_abort = 1;
+              atomicExch(T.err, 1);
+            }
+          } else {
+            ok = false;
+          }
+          C v0 = czero<float>(), v1 = v0;
+          if (ok) {
+            const unsigned char* base = smem + (size_t)st * L::STAGE;
+            const C* A = reinterpret_cast<const C*>(base);
+            const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
+            const int kq = z0 - 1 + q;
+            const bool mine = own && kq >= z0 && kq < z1;
+            const float4 a = ld4(A + o);
+            v0 = lo2(a);
+            v1 = hi2(a);
+            if (hasB) {
+              const float4 bb = ld4(B + o);
+              v0 = fma_c(coef, lo2(bb), v0);
+              v1 = fma_c(coef, hi2(bb), v1);
+              if (MODE == M_P1 && hasX && mine) {
+                const float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
+                st4(pX + po, fma_c(xal, lo2(bb), lo2(xv)), fma_c(xal, hi2(bb), hi2(xv)));
+              }
+            }
+            if (mine) st4(pF + po, v0, v1);
+            if (q >= 2 && own) {
+              // plane kq-1: add the z+1 term (this plane's own F) to the pending partial stencil
+              C a0 = p0 + c0 * v0, a1 = p1 + c1 * v1;
+              if (MODE == M_P1 && kq - 1 == src_k) {
+                if (src_lane == 0) a0 = czero<float>();
+                if (src_lane == 1) a1 = czero<float>();
+              }
+              if (MODE == M_P2 && pG) {
+                // refinement inner solve: s = S^H r + S^H r64
+                const float4 gv = __ldg(reinterpret_cast<const float4*>(pG + po - plane));
+                a0 = a0 + lo2(gv);
+                a1 = a1 + hi2(gv);
+              }
+              st4(pO + po - plane, a0, a1);
+              accf += abs2(a0) + abs2(a1);
+            }
+            if (q >= 1 && q <= count - 2) {
+              // plane kq: every stencil term but the z+1 one, from this stage and registers
+              const float2 mk = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base + L::OFF_M) + oc);
+              C l = A[o - 1], r = A[o + 2];
+              float4 ym = ld4(A + o - L::HW), yp = ld4(A + o + L::HW);
+              C ym0 = lo2(ym), ym1 = hi2(ym), yp0 = lo2(yp), yp1 = hi2(yp);
+              if (hasB) {
+                l = fma_c(coef, B[o - 1], l);
+                r = fma_c(coef, B[o + 2], r);
+                const float4 bym = ld4(B + o - L::HW), byp = ld4(B + o + L::HW);
+                ym0 = fma_c(coef, lo2(bym), ym0);
+                ym1 = fma_c(coef, hi2(bym), ym1);
+                yp0 = fma_c(coef, lo2(byp), yp0);
+                yp1 = fma_c(coef, hi2(byp), yp1);
+              }
+              const C zero = czero<float>();
+              const int var = xpf | ypf | ((kq >= zlo && kq <= zhi) ? 0 : 1);
+              if (var == 0) {
+                p0 = stencil_interior<float>(ih2, om2 * mk.x, v0, l, v1, ym0, yp0, fc0, zero);
+                p1 = stencil_interior<float>(ih2, om2 * mk.y, v1, v0, r, ym1, yp1, fc1, zero);
+                c0 = c1 = mkc(ih2, 0.f);
+              } else {
+                C sx0 = mkc(1.f, 0.f), sx1 = sx0, ixa = mkc(ih2, 0.f), ixb = ixa, ixc = ixa;
+                C sy = mkc(1.f, 0.f), iym = mkc(ih2, 0.f), iyp = iym;
+                C sz = mkc(1.f, 0.f), izm = mkc(ih2, 0.f), izp = izm;
+                if (var & 4) {
+                  sx0 = xs_tab[2 * tx];
+                  sx1 = xs_tab[2 * tx + 1];
+                  ixa = xh_tab[2 * tx];
+                  ixb = xh_tab[2 * tx + 1];
+                  ixc = xh_tab[2 * tx + 2];
+                }
+                if (var & 2) {
+                  sy = ys_tab[ty];
+                  iym = yh_tab[ty];
+                  iyp = yh_tab[ty + 1];
+                }
+                if (var & 1) {
+                  const C* zr = ztab + 3 * kq;
+                  sz = __ldg(zr);
+                  izm = __ldg(zr + 1);
+                  izp = __ldg(zr + 2);
+                }
+                const float om0 = om2 * mk.x, om1 = om2 * mk.y;
+#define WRI_AX(AX_, AY_, AZ_)                                                                                       \
+  p0 = stencil_axes<AX_, AY_, AZ_>(ih2, om0, v0, l, v1, ym0, yp0, fc0, zero, sx0, ixa, ixb, sy, iym, iyp, sz, izm,    \
+                                   izp);                                                                            \
+  p1 = stencil_axes<AX_, AY_, AZ_>(ih2, om1, v1, v0, r, ym1, yp1, fc1, zero, sx1, ixb, ixc, sy, iym, iyp, sz, izm,    \
+                                   izp);
+                switch (var) {
+                  case 1: WRI_AX(false, false, true) break;
+                  case 2: WRI_AX(false, true, false) break;
+                  case 3: WRI_AX(false, true, true) break;
+                  case 4: WRI_AX(true, false, false) break;
+                  case 5: WRI_AX(true, false, true) break;
+                  case 6: WRI_AX(true, true, false) break;
+                  default: WRI_AX(true, true, true) break;
+                }
+#undef WRI_AX
+                // coefficient of the z+1 neighbour: (s_x s_y of the stretched axes) x (1/(s_z h^2) or 1/h^2)
+                const C zc = (var & 1) ? izp : mkc(ih2, 0.f);
+                const C syz = (var & 2) ? sy * zc : zc;
+                c0 = (var & 4) ? sx0 * syz : syz;
+                c1 = (var & 4) ? sx1 * syz : syz;
+              }
+            }
+          }
+          if ((q & 3) == 3) {
+            accd += (double)accf;
+            accf = 0.f;
+          }
+          // this plane's stage is no longer needed: hand it back to the copy warp
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[st]);
+          fc0 = v0;
+          fc1 = v1;
+        }
+        fills += (unsigned)count;
+        accd += (double)accf;
+      } else {
       C fm0 = czero<float>(), fm1 = fm0, fc0 = fm0, fc1 = fm0;  // own F of planes kq-2, kq-1
       float2 m_c = make_float2(0.f, 0.f);                        // m of plane kq-1
       long long po = (long long)(z0 - 1) * plane;
@@ -1098,6 +1238,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
       if (lane == 0) mbar_arrive(&empty[(fills + count - 1) % S]);
       fills += (unsigned)count;
       accd += (double)accf;
+      }  // ER
     }
 
     // ---- tile partial, ticket and the system's finalizer (consumer threads only)
