@@ -1074,7 +1074,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
     return WRI_ECUDA;
   }
   static const int kCfgs[] = {8, 9, 12, 13, 17, 18};
-  static const int kOrders[] = {0, 5, 6};
+  static const int kOrders[] = {2, 5, 6};  // systems of a tile consecutive, blocks of 8, blocks of 16
   float best = 0.f;
   int best_kernel = 0, best_order = 0;
   rc = WRI_OK;
