@@ -1,0 +1,139 @@
+"""Source-free adaptive WRI outer loop (Algorithm 2, without the TV term).
+
+Every outer iteration evaluates the reduced objective f4 and its gradient g4 (Eqs. VarObj2 and
+VarG2) with the augmented systems solved to the current tolerance eps, takes the l-BFGS step
+m~ = m - H g, and evaluates f4 at m~ with the same eps.  A step that does not decrease f4 is
+not taken: eps is halved, f4 and g4 are evaluated again at the same model, and the step is
+recomputed.  The objective and gradient come from ``objective.py`` (libwri's kernels); this
+module is host-side control flow plus a few vector operations on the model.
+
+Readings (the paper states none of these):
+  * eps is the relative normal-equation residual of the CGLS solves (and the FP64 refinement's
+    target when refinement is on);
+  * l-BFGS keeps the last ``memory`` (s, y) pairs of accepted steps (curvature s.y > 0 only);
+    H0 = (s.y / y.y) I from the newest pair; before the first pair H0 = eta I with eta such that
+    the first step changes m by ``first_step`` times max |m| at most;
+  * the step is taken in full (Algorithm 2 has no line search);
+  * the evaluation at an accepted m~ is reused as the next iteration's first evaluation (it is
+    the same solve at the same model and tolerance);
+  * if a step fails with eps already below ``eps_min`` the loop stops (status "eps_min").
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Tuple
+
+import torch
+
+
+class LBFGS:
+    """Limited-memory BFGS inverse-Hessian product by the two-loop recursion."""
+
+    def __init__(self, memory: int = 5):
+        if memory < 1:
+            raise ValueError("memory >= 1")
+        self.memory = memory
+        self.s: List[torch.Tensor] = []
+        self.y: List[torch.Tensor] = []
+
+    def update(self, s: torch.Tensor, y: torch.Tensor) -> bool:
+        """Store the pair if it satisfies the curvature condition; returns whether it was kept."""
+        sy = float(torch.dot(s.ravel(), y.ravel()))
+        if not sy > 1e-12 * float(s.norm()) * float(y.norm()):
+            return False
+        self.s.append(s.clone())
+        self.y.append(y.clone())
+        if len(self.s) > self.memory:
+            self.s.pop(0)
+            self.y.pop(0)
+        return True
+
+    def apply(self, g: torch.Tensor, h0: Optional[float] = None) -> torch.Tensor:
+        """H g.  h0 scales the initial matrix when no pair is stored (required then)."""
+        q = g.clone()
+        if not self.s:
+            if h0 is None:
+                raise ValueError("h0 is needed before the first pair")
+            return h0 * q
+        rho = [1.0 / float(torch.dot(s.ravel(), y.ravel())) for s, y in zip(self.s, self.y)]
+        a = [0.0] * len(self.s)
+        for i in range(len(self.s) - 1, -1, -1):
+            a[i] = rho[i] * float(torch.dot(self.s[i].ravel(), q.ravel()))
+            q -= a[i] * self.y[i]
+        sn, yn = self.s[-1], self.y[-1]
+        r = (float(torch.dot(sn.ravel(), yn.ravel())) / float(torch.dot(yn.ravel(), yn.ravel()))) * q
+        for i in range(len(self.s)):
+            bcoef = rho[i] * float(torch.dot(self.y[i].ravel(), r.ravel()))
+            r += (a[i] - bcoef) * self.s[i]
+        return r
+
+
+@dataclass
+class AwriResult:
+    m: torch.Tensor
+    f: float
+    status: str                                    # "n_iter" or "eps_min"
+    history: List[dict] = field(default_factory=list)
+    evaluations: int = 0
+
+
+def awri(m0: torch.Tensor, evaluate: Callable[[torch.Tensor, float], Tuple[float, torch.Tensor]],
+         eps0: float, n_iter: int, eps_min: float = 1e-12, memory: int = 5, first_step: float = 0.05,
+         model_error: Optional[Callable[[torch.Tensor], float]] = None) -> AwriResult:
+    """Algorithm 2 (gamma = 0).  ``evaluate(m, eps) -> (f, g)`` gives f4 and g4 at m with the
+    systems solved to tolerance eps (e.g. ``make_evaluate``)."""
+    if not (eps0 > 0 and n_iter >= 0):
+        raise ValueError("eps0 > 0 and n_iter >= 0 required")
+    m = m0.detach().clone().to(torch.float64)
+    eps = float(eps0)
+    lb = LBFGS(memory)
+    f, g = evaluate(m, eps)
+    evals = 1
+    hist = []
+    status = "n_iter"
+    for k in range(n_iter):
+        while True:
+            h0 = None
+            if not lb.s:
+                gmax = float(g.abs().max())
+                h0 = first_step * float(m.abs().max()) / gmax if gmax > 0 else 0.0
+            m_t = m - lb.apply(g, h0)
+            f_t, g_t = evaluate(m_t, eps)
+            evals += 1
+            if f_t <= f:
+                break
+            if 0.5 * eps < eps_min:
+                status = "eps_min"
+                break
+            eps *= 0.5                       # reduce the tolerance and recompute at m^(k)
+            f, g = evaluate(m, eps)
+            evals += 1
+        if status == "eps_min":
+            break
+        lb.update(m_t - m, g_t - g)
+        m, f, g = m_t, f_t, g_t
+        rec = {"iteration": k + 1, "f": f, "eps": eps, "evaluations": evals}
+        if model_error is not None:
+            rec["model_error"] = float(model_error(m))
+        hist.append(rec)
+    return AwriResult(m=m, f=f, status=status, history=hist, evaluations=evals)
+
+
+def make_evaluate(groups, opts, max_resident: int = 1 << 30, stats: Optional[dict] = None):
+    """evaluate(m, eps) for ``awri`` on libwri: the solves of ``objective.objective`` with tolerance
+    eps (and FP64 refinement target eps when ``opts`` refines); returns (f, g) with g float64."""
+    from . import objective as obj
+    from . import wri
+
+    def evaluate(m: torch.Tensor, eps: float):
+        o = wri.WriSolveOpts.from_buffer_copy(opts)
+        o.tol = float(eps)
+        if int(o.max_refine) > 0:
+            o.refine_tol = float(eps)
+        mm = m.detach().clone().requires_grad_(True)
+        st = {} if stats is None else stats
+        f = obj.objective(mm, groups, o, max_resident=max_resident, stats=st)
+        f.backward()
+        return float(f.item()), mm.grad.detach().to(torch.float64)
+
+    return evaluate

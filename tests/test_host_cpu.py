@@ -84,3 +84,56 @@ def test_workload_shards_differ_only_in_weights_and_data():
     b = synth.workload_c4(nsrc=4, freqs=((3.0, 16),), nrec=8, shard=1)[0]
     assert np.array_equal(a.src, b.src) and np.array_equal(a.rec_idx, b.rec_idx) and np.array_equal(a.m, b.m)
     assert not np.allclose(a.alpha, b.alpha) and not np.allclose(a.d, b.d)
+
+
+def test_lbfgs_product_matches_oracle_two_loop():
+    """The product's l-BFGS product (torch) equals the oracle's two-loop recursion (numpy)."""
+    from oracle.awri_oracle import two_loop
+    from paper_2410_18429_gb300.awri import LBFGS
+    r = np.random.Generator(np.random.PCG64(41))
+    n = 15
+    Q = r.standard_normal((n, n))
+    Q = Q @ Q.T + n * np.eye(n)
+    lb = LBFGS(memory=3)
+    S, Y = [], []
+    for _ in range(5):
+        s = r.standard_normal(n)
+        y = Q @ s
+        assert lb.update(torch.as_tensor(s), torch.as_tensor(y))
+        S.append(s)
+        Y.append(y)
+    g = r.standard_normal(n)
+    got = lb.apply(torch.as_tensor(g)).numpy()
+    assert np.allclose(got, two_loop(g, S[-3:], Y[-3:]), rtol=1e-12, atol=1e-14)
+    assert not lb.update(torch.as_tensor(S[0]), torch.as_tensor(-Y[0]))   # s.y < 0: refused
+
+
+def test_awri_product_loop_matches_oracle_loop():
+    """The product's Algorithm 2 control flow (tolerance halving, acceptance, l-BFGS pairs) gives
+    the oracle's iterates on the same objective, including halvings."""
+    from oracle.awri_oracle import awri as awri_oracle
+    from paper_2410_18429_gb300.awri import awri
+    r = np.random.Generator(np.random.PCG64(7))
+    n = 10
+    U, _ = np.linalg.qr(r.standard_normal((n, n)))
+    Q = U @ np.diag(np.linspace(1.0, 30.0, n)) @ U.T
+    m_star = r.uniform(1.0, 2.0, n)
+    c = r.standard_normal(n)
+
+    def f_np(m, eps):
+        # exact objective, gradient with an eps-sized error (as from loosely solved systems)
+        e = m - m_star
+        return 0.5 * e @ Q @ e, Q @ e + 200.0 * eps * c
+
+    def f_torch(m, eps):
+        f, g = f_np(m.numpy(), eps)
+        return float(f), torch.as_tensor(g)
+
+    m0 = np.full(n, 1.5)
+    mo, fo, so, ho = awri_oracle(m0, f_np, 0.2, 8, first_step=0.3, eps_min=1e-6)
+    res = awri(torch.as_tensor(m0), f_torch, 0.2, 8, first_step=0.3, eps_min=1e-6)
+    assert res.status == so
+    assert [h["eps"] for h in res.history] == [h["eps"] for h in ho]
+    assert any(h["eps"] < 0.2 for h in ho)           # the case exercises the halving
+    assert np.allclose(res.m.numpy(), mo, rtol=1e-12, atol=1e-14)
+    assert abs(res.f - fo) <= 1e-12 * abs(fo)

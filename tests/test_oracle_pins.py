@@ -263,3 +263,62 @@ def test_gradient_matches_central_differences(source_free):
         fd = (fp - fm) / (2 * eps)
         an = float(g @ dm.ravel())
         assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+# ---------------------------------------------------------------- outer loop (Algorithm 2)
+def test_two_loop_recursion_equals_dense_bfgs_inverse():
+    """The l-BFGS two-loop product equals the dense inverse-Hessian BFGS update applied to g."""
+    from oracle.awri_oracle import bfgs_inverse, two_loop
+    r = synth.rng(23)
+    n = 9
+    Q = r.standard_normal((n, n))
+    Q = Q @ Q.T + n * np.eye(n)
+    S = [r.standard_normal(n) for _ in range(4)]
+    Y = [Q @ s for s in S]                       # curvature pairs of a convex quadratic (s.y > 0)
+    g = r.standard_normal(n)
+    assert np.allclose(two_loop(g, S, Y), bfgs_inverse(S, Y) @ g, rtol=1e-12, atol=1e-12)
+    # with one pair the inverse Hessian maps y to s (secant condition)
+    assert np.allclose(two_loop(Y[-1], S[-1:], Y[-1:]), S[-1], rtol=1e-12)
+
+
+def test_awri_oracle_minimises_a_convex_quadratic():
+    """With exact evaluations Algorithm 2 reduces to full-step l-BFGS: on a well-conditioned
+    quadratic the first 10 steps all decrease f and close in on the minimiser, and eps is never
+    halved.  (Without a line search a later full step can fail; halving eps cannot help exact
+    evaluations, so the loop then ends at eps_min, as the adaptive rule prescribes.)"""
+    from oracle.awri_oracle import awri
+    r = synth.rng(5)
+    n = 12
+    U, _ = np.linalg.qr(r.standard_normal((n, n)))
+    Q = U @ np.diag(np.linspace(1.0, 10.0, n)) @ U.T
+    m_star = r.uniform(1.0, 2.0, n)
+
+    def evaluate(m, eps):
+        e = m - m_star
+        return 0.5 * e @ Q @ e, Q @ e
+
+    m0 = np.full(n, 1.5)
+    m, f, status, hist = awri(m0, evaluate, 1e-2, 10, first_step=0.05)
+    assert status == "n_iter" and len(hist) == 10
+    assert np.linalg.norm(m - m_star) < 1e-3 * np.linalg.norm(m0 - m_star)
+    assert all(h["eps"] == 1e-2 for h in hist)
+    assert all(a["f"] > b["f"] for a, b in zip(hist, hist[1:]))
+
+
+def test_awri_oracle_halves_eps_until_the_step_decreases_f():
+    """The adaptive rule: a step whose objective (at the current eps) does not decrease is
+    refused, eps is halved and f, g are evaluated again at the same model."""
+    from oracle.awri_oracle import awri
+    calls = []
+
+    def evaluate(m, eps):
+        calls.append(eps)
+        # exact part 1/2 |m|^2, plus an eps-sized bias that grows away from the start point
+        return 0.5 * m @ m + 50.0 * eps * abs(m[0] - 1.0), m.copy()
+
+    m, f, status, hist = awri(np.array([1.0, 1.0]), evaluate, 0.1, 1, first_step=0.5)
+    # eps 0.1: f~ = 0.25 + 2.5 > 1.0 -> halve; 0.05: 0.25 + 1.25 > 1.0 -> halve; 0.025: accept
+    assert calls == [0.1, 0.1, 0.05, 0.05, 0.025, 0.025]
+    assert hist == [{"iteration": 1, "f": 0.25 + 50.0 * 0.025 * 0.5, "eps": 0.025}]
+    m, f, status, hist = awri(np.array([1.0, 1.0]), evaluate, 0.1, 1, first_step=0.5, eps_min=0.04)
+    assert status == "eps_min" and hist == []
