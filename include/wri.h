@@ -209,6 +209,18 @@ WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype
 WRI_API int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int trial_iters,
                          void* workspace, size_t ws_bytes, wri_stream_t stream);
 
+/* Total-variation term of Eq. TVAWRI, for the outer loop (Algorithm 2), not the solve.  Our
+ * reading of the paper's ||m||_TV: the smoothed isotropic TV
+ *     TV(m) = sum over nodes of sqrt(dx^2 + dy^2 + dz^2 + beta^2),
+ * forward differences in grid units (dx = m[i+1] - m[i], zero on the last node of an axis).
+ *   m    device [n] double on the grid of `grid` (only nx, ny, nz are used; the grid must be
+ *        valid as for the other calls)
+ *   tv   device [1] double: tv += gamma TV(m) (FP64 atomics: last-bit order dependence)
+ *   grad device [n] double: grad += gamma dTV/dm, or NULL
+ * beta > 0 and gamma >= 0 (WRI_EINVAL otherwise).  Enqueued on `stream`. */
+WRI_API int wri_tv(const wri_grid* grid, const double* m, double beta, double gamma, double* tv, double* grad,
+                   wri_stream_t stream);
+
 /* Number of built tile configurations of the z-march kernels and the thread-block shape of one
  * of them (tile = 1..count; WRI_EINVAL otherwise).  Outside the paper: an implementation
  * choice exposed for tuning. */

@@ -16,6 +16,7 @@ from __future__ import annotations
 import numpy as np
 
 from .wri_oracle import evaluate as _evaluate
+from .wri_oracle import total_variation as _total_variation
 
 __all__ = ["two_loop", "bfgs_inverse", "awri", "exact_evaluate"]
 
@@ -51,14 +52,20 @@ def bfgs_inverse(S, Y):
     return H
 
 
-def exact_evaluate(G, d, lam=None, source_free=True):
-    """evaluate(m, eps) -> (f4, g4) of one frequency group by exact solves (eps unused)."""
+def exact_evaluate(G, d, lam=None, source_free=True, tv_gamma=0.0, tv_beta=1e-9):
+    """evaluate(m, eps) -> (f4 + tv_gamma TV, g4 + tv_gamma dTV/dm) of one frequency group by
+    exact solves (eps unused); TV is ``total_variation`` (Eq. TVAWRI, our reading)."""
     lam = G.lam if lam is None else lam
 
     def evaluate(m, eps):
-        _, _, f, g = _evaluate(G.spec.shape, G.spec.h, G.omega, np.asarray(m).reshape(G.spec.shape), G.spec.npml,
+        mm = np.asarray(m).reshape(G.spec.shape)
+        _, _, f, g = _evaluate(G.spec.shape, G.spec.h, G.omega, mm, G.spec.npml,
                                G.v_max, G.src, G.rec_off, G.rec_idx, d, lam, alpha=None if source_free else G.alpha,
                                source_free=source_free)
+        if tv_gamma > 0:
+            tv, gtv = _total_variation(mm, tv_beta)
+            f = f + tv_gamma * tv
+            g = g + tv_gamma * gtv.ravel()
         return f, g
 
     return evaluate

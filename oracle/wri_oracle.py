@@ -36,7 +36,7 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "stretch", "helmholtz_matrix", "apply_helmholtz", "restriction", "unit_vector",
     "augmented_operator", "rhs", "solve_kkt", "solve_dataspace", "solve_dense", "stretch_weight", "cgls", "source_estimate",
-    "objective", "gradient", "solve_system", "evaluate", "forward_data",
+    "objective", "gradient", "solve_system", "evaluate", "forward_data", "total_variation",
 ]
 
 
@@ -332,3 +332,36 @@ def forward_data(shape, h, omega, m_true, npml, v_max, srcs, rec_off, rec_idx, a
         u = lu.solve(alpha[s] * unit_vector(n, srcs[s]))
         out[rec_off[s]:rec_off[s + 1]] = u[rec_idx[rec_off[s]:rec_off[s + 1]]]
     return out
+
+
+# --------------------------------------------------------------------------------------
+# Total-variation term of Eq. TVAWRI (our reading of the paper's ||m||_TV)
+# --------------------------------------------------------------------------------------
+def total_variation(m, beta):
+    """Smoothed isotropic TV of a model on its grid and its gradient.
+
+    TV(m) = sum over nodes of sqrt(dx^2 + dy^2 + dz^2 + beta^2), with forward differences in
+    grid units (dx = m[i+1] - m[i], zero on the last node of an axis).  The gradient is the
+    derivative of that sum; the paper's weight gamma multiplies both.  Returns (TV, grad).
+    """
+    m = np.asarray(m, dtype=np.float64)
+    d = []
+    for ax in range(3):
+        da = np.zeros_like(m)
+        sl_hi = [slice(None)] * 3
+        sl_lo = [slice(None)] * 3
+        sl_hi[ax] = slice(1, None)
+        sl_lo[ax] = slice(0, -1)
+        da[tuple(sl_lo)] = m[tuple(sl_hi)] - m[tuple(sl_lo)]
+        d.append(da)
+    q = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2 + beta ** 2)
+    grad = np.zeros_like(m)
+    for ax in range(3):
+        w = d[ax] / q                     # derivative of q with respect to the difference
+        sl_hi = [slice(None)] * 3
+        sl_lo = [slice(None)] * 3
+        sl_hi[ax] = slice(1, None)
+        sl_lo[ax] = slice(0, -1)
+        grad[tuple(sl_lo)] -= w[tuple(sl_lo)]
+        grad[tuple(sl_hi)] += w[tuple(sl_lo)]
+    return float(q.sum()), grad

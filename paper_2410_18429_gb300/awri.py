@@ -1,4 +1,4 @@
-"""Source-free adaptive WRI outer loop (Algorithm 2, without the TV term).
+"""Source-free adaptive WRI outer loop (Algorithm 2), with the TV term of Eq. TVAWRI optional.
 
 Every outer iteration evaluates the reduced objective f4 and its gradient g4 (Eqs. VarObj2 and
 VarG2) with the augmented systems solved to the current tolerance eps, takes the l-BFGS step
@@ -119,9 +119,11 @@ def awri(m0: torch.Tensor, evaluate: Callable[[torch.Tensor, float], Tuple[float
     return AwriResult(m=m, f=f, status=status, history=hist, evaluations=evals)
 
 
-def make_evaluate(groups, opts, max_resident: int = 1 << 30, stats: Optional[dict] = None):
+def make_evaluate(groups, opts, max_resident: int = 1 << 30, stats: Optional[dict] = None, tv_gamma: float = 0.0,
+                  tv_beta: float = 1e-9):
     """evaluate(m, eps) for ``awri`` on libwri: the solves of ``objective.objective`` with tolerance
-    eps (and FP64 refinement target eps when ``opts`` refines); returns (f, g) with g float64."""
+    eps (and FP64 refinement target eps when ``opts`` refines), plus tv_gamma times the TV term
+    of Eq. TVAWRI (``wri_tv``, smoothing tv_beta) when tv_gamma > 0; returns (f, g), g float64."""
     from . import objective as obj
     from . import wri
 
@@ -134,6 +136,10 @@ def make_evaluate(groups, opts, max_resident: int = 1 << 30, stats: Optional[dic
         st = {} if stats is None else stats
         f = obj.objective(mm, groups, o, max_resident=max_resident, stats=st)
         f.backward()
-        return float(f.item()), mm.grad.detach().to(torch.float64)
+        fv, g = float(f.item()), mm.grad.detach().to(torch.float64)
+        if tv_gamma > 0:
+            tv, _ = wri.tv(groups[0], m, tv_beta, tv_gamma, grad=g)
+            fv += float(tv.item())
+        return fv, g
 
     return evaluate

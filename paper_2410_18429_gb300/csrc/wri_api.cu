@@ -1119,6 +1119,14 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
   return WRI_OK;
 }
 
+int wri_tv(const wri_grid* grid, const double* m, double beta, double gamma, double* tv, double* grad,
+           wri_stream_t stream) {
+  if (!grid_valid(grid) || !m || !tv) return WRI_EINVAL;
+  if (!(beta > 0) || !std::isfinite(beta) || !(gamma >= 0) || !std::isfinite(gamma)) return WRI_EINVAL;
+  WRI_CK(launch_tv(m, grid->nx, grid->ny, grid->nz, beta, gamma, tv, grad, (cudaStream_t)stream));
+  return WRI_OK;
+}
+
 int wri_tile_count(void) { return 3; }
 
 int wri_tile_shape(int tile, int* bx, int* by) {

@@ -28,6 +28,8 @@ cudaError_t launch_ir_final(const Batch& b, void* const* u, cudaStream_t st);
 cudaError_t launch_source_estimate(int rbytes, const Batch& b, int nsys_total, double* alpha_out, cudaStream_t st);
 cudaError_t launch_data_term(int rbytes, int dbytes, const Batch& b, int nsys_total, cudaStream_t st);
 cudaError_t launch_widen(const void* u, void* u64, long long count, cudaStream_t st);
+cudaError_t launch_tv(const double* m, int nx, int ny, int nz, double beta, double gamma, double* tv, double* grad,
+                      cudaStream_t st);
 
 // unfused baseline kernels (wri_small.cu); pointers are complex of element size rbytes
 cudaError_t plain_fill(int rbytes, void* r1, void* x, long long n, long long src, double ar, double ai,

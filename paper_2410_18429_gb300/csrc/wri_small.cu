@@ -79,6 +79,13 @@ cudaError_t launch_data_term(int rbytes, int dbytes, const Batch& b, int nsys_to
   return cudaGetLastError();
 }
 
+cudaError_t launch_tv(const double* m, int nx, int ny, int nz, double beta, double gamma, double* tv, double* grad,
+                      cudaStream_t st) {
+  const long long n = (long long)nx * ny * nz;
+  k_tv<<<grid_for(n, 256, 4096), 256, 0, st>>>(m, nx, ny, nz, beta, gamma, tv, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_widen(const void* u, void* u64, long long count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   k_widen<<<grid_for(count, 256), 256, 0, st>>>((const float2*)u, (double2*)u64, count);

@@ -229,6 +229,63 @@ __global__ void k_widen(const float2* u, double2* u64, long long count) {
     u64[e] = make_double2(u[e].x, u[e].y);
 }
 
+// ------------------------------------------------------------------ total variation (Eq. TVAWRI)
+// Smoothed isotropic TV of a model on its grid (our reading of ||m||_TV):
+//   TV(m) = sum over nodes of sqrt(dx^2 + dy^2 + dz^2 + beta^2),
+// forward differences in grid units (dx = m[i+1] - m[i]; zero on the last node of an axis).
+// tv += gamma TV(m); grad (if not null) += gamma dTV/dm.  One thread per node, grid-stride.
+__device__ __forceinline__ double tv_cell(const double* m, int nx, int ny, int nz, int i, int j, int k,
+                                          double beta2, double& dx, double& dy, double& dz) {
+  const long long plane = (long long)nx * ny;
+  const long long c = (long long)k * plane + (long long)j * nx + i;
+  const double v = m[c];
+  dx = (i + 1 < nx) ? m[c + 1] - v : 0.0;
+  dy = (j + 1 < ny) ? m[c + nx] - v : 0.0;
+  dz = (k + 1 < nz) ? m[c + plane] - v : 0.0;
+  return sqrt(dx * dx + dy * dy + dz * dz + beta2);
+}
+
+__global__ void k_tv(const double* m, int nx, int ny, int nz, double beta, double gamma, double* tv, double* grad) {
+  __shared__ double red[8];
+  const long long n = (long long)nx * ny * nz;
+  const double beta2 = beta * beta;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / ((long long)nx * ny));
+    const long long rem = e - (long long)k * nx * ny;
+    const int j = (int)(rem / nx);
+    const int i = (int)(rem - (long long)j * nx);
+    double dx, dy, dz;
+    const double q = tv_cell(m, nx, ny, nz, i, j, k, beta2, dx, dy, dz);
+    acc += q;
+    if (grad) {
+      double gsum = -(dx + dy + dz) / q;  // this node's own cell
+      double ax, ay, az;
+      if (i > 0) {  // the cell of node i-1, whose x difference contains this node
+        const double qq = tv_cell(m, nx, ny, nz, i - 1, j, k, beta2, ax, ay, az);
+        gsum += ax / qq;
+      }
+      if (j > 0) {
+        const double qq = tv_cell(m, nx, ny, nz, i, j - 1, k, beta2, ax, ay, az);
+        gsum += ay / qq;
+      }
+      if (k > 0) {
+        const double qq = tv_cell(m, nx, ny, nz, i, j, k - 1, beta2, ax, ay, az);
+        gsum += az / qq;
+      }
+      grad[e] += gamma * gsum;
+    }
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    if (t != 0.0) atomicAdd(tv, gamma * t);
+  }
+}
+
 // ------------------------------------------------------------------ unfused baseline kernels
 template <typename R>
 __global__ void k_p_fill(cx<R>* r1, cx<R>* x, long long n, long long src, cx<R> a_src) {

@@ -64,13 +64,14 @@ def _load():
     lib.wri_gradient.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp, sz, vp]
     lib.wri_gradient_noalloc.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp]
     lib.wri_autotune.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), i32, vp, sz, vp]
+    lib.wri_tv.argtypes = [C.POINTER(WriGrid), dp, C.c_double, C.c_double, dp, dp, vp]
     lib.wri_tile_count.argtypes = []
     lib.wri_tile_shape.argtypes = [i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.wri_strerror.argtypes = [i32]
     lib.wri_strerror.restype = C.c_char_p
     lib.wri_version.restype = C.c_char_p
     for f in ("wri_apply_A", "wri_apply_AH", "wri_solve_batch", "wri_source_estimate", "wri_gradient",
-              "wri_gradient_noalloc", "wri_autotune", "wri_tile_count", "wri_tile_shape"):
+              "wri_gradient_noalloc", "wri_autotune", "wri_tv", "wri_tile_count", "wri_tile_shape"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -78,7 +79,7 @@ def _load():
 lib = _load()
 
 EXPORTS = ("wri_apply_A", "wri_apply_AH", "wri_workspace_size", "wri_aux_workspace_size", "wri_solve_batch",
-           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_autotune", "wri_tile_count",
+           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_autotune", "wri_tv", "wri_tile_count",
            "wri_tile_shape", "wri_strerror", "wri_version")
 
 
@@ -288,6 +289,20 @@ def autotune(groups: Sequence[GroupSpec], opts: WriSolveOpts, trial_iters: int =
     _check(lib.wri_autotune(m.arr, m.n, C.byref(out), int(trial_iters), _ptr(ws), ws.numel(), _stream(stream)),
            "wri_autotune")
     return out
+
+
+def tv(g: GroupSpec, m, beta: float, gamma: float = 1.0, out=None, grad=None, stream=None):
+    """wri_tv: (tv [1] float64, grad) with tv += gamma TV(m) and grad += gamma dTV/dm (if given).
+
+    m: float64 CUDA tensor shaped like the group's grid."""
+    import torch
+    mm = m.detach().to(torch.float64).contiguous()
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device=mm.device)
+    grid = g.grid()
+    _check(lib.wri_tv(C.byref(grid), _ptr(mm), float(beta), float(gamma), _ptr(out), _ptr(grad), _stream(stream)),
+           "wri_tv")
+    return out, grad
 
 
 def tile_shapes():

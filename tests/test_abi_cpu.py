@@ -143,3 +143,13 @@ def test_fp64_wavefield_must_be_on_every_group_and_aligned(W):
     assert W.lib.wri_source_estimate(m.arr, 2, W.C64, 0x3000, 0x1000, 1 << 30, None) == W.EINVAL
     o = W.make_opts()
     assert W.lib.wri_solve_batch(m.arr, 2, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 40, None) == W.EINVAL
+
+
+def test_tv_rejects_invalid_arguments(W):
+    g = W.WriGrid(20, 18, 16, 3, 10.0, 60.0, 1e-3, 2000.0)
+    assert W.lib.wri_tv(C.byref(g), 0x1000, 0.0, 1.0, 0x2000, None, None) == W.EINVAL      # beta = 0
+    assert W.lib.wri_tv(C.byref(g), 0x1000, 0.1, -1.0, 0x2000, None, None) == W.EINVAL     # gamma < 0
+    assert W.lib.wri_tv(C.byref(g), None, 0.1, 1.0, 0x2000, None, None) == W.EINVAL        # no model
+    assert W.lib.wri_tv(C.byref(g), 0x1000, 0.1, 1.0, None, None, None) == W.EINVAL        # no output
+    g2 = W.WriGrid(2, 18, 16, 0, 10.0, 60.0, 1e-3, 2000.0)
+    assert W.lib.wri_tv(C.byref(g2), 0x1000, 0.1, 1.0, 0x2000, None, None) == W.EINVAL

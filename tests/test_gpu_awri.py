@@ -80,3 +80,42 @@ def test_awri_adaptive_c64_decreases_objective(W):
     assert all(a >= b for a, b in zip(eps, eps[1:])) and all(e in [1e-2 * 0.5 ** k for k in range(20)] for e in eps)
     # the model error is tracked (at this loose tolerance it need not fall: the paper adds TV for that)
     assert all(np.isfinite(h["model_error"]) for h in res.history)
+
+
+@pytest.mark.parametrize("shape", [(14, 16, 18), (20, 30, 40)])
+def test_tv_kernel_matches_oracle(W, shape):
+    """wri_tv against the oracle's total variation: value and gradient, accumulated (+=)."""
+    wri, _ = W
+    from paper_2410_18429_gb300.problem import to_device
+    G = synth.workload_small(nphys=(shape[2] - 6, shape[1] - 6, shape[0] - 6), npml=3, nsys=1, seed=3, nrec=4)
+    spec = to_device(G, wri.C128, "cuda")
+    r = synth.rng(12)
+    m = r.standard_normal(shape).cumsum(axis=2) * 1e-8 + 2.5e-7     # a rough but correlated model
+    tv_ref, g_ref = O.total_variation(m, 3e-9)
+    mt = torch.as_tensor(m).cuda()
+    grad = torch.zeros_like(mt)
+    tv, _ = wri.tv(spec, mt, 3e-9, 0.7, grad=grad)
+    assert abs(tv.item() - 0.7 * tv_ref) <= 1e-12 * abs(0.7 * tv_ref)
+    assert rel(grad.cpu().numpy(), 0.7 * g_ref) < 1e-12
+    wri.tv(spec, mt, 3e-9, 0.7, out=tv, grad=grad)                    # accumulates
+    assert abs(tv.item() - 1.4 * tv_ref) <= 1e-12 * abs(1.4 * tv_ref)
+    assert rel(grad.cpu().numpy(), 1.4 * g_ref) < 1e-12
+
+
+def test_awri_with_tv_c128_matches_oracle_loop(W):
+    """Algorithm 2 with the TV term of Eq. TVAWRI (gamma = 0.02, beta = 1e-9): libwri's loop
+    reproduces the oracle's on exact solves."""
+    wri, awri = W
+    from oracle.awri_oracle import awri as awri_oracle
+    from oracle.awri_oracle import exact_evaluate
+    from paper_2410_18429_gb300.problem import to_device
+    G, d, m_true, m0 = _inversion_case()
+    groups = [to_device(G, wri.C128, "cuda", d=d)]
+    ev = awri.make_evaluate(groups, wri.make_opts(tol=1e-11, max_iter=400000, dtype=wri.C128), tv_gamma=0.02,
+                            tv_beta=1e-9)
+    res = awri.awri(torch.as_tensor(m0).cuda(), ev, 1e-11, 3, eps_min=1e-13, first_step=0.02)
+    mo, fo, so, ho = awri_oracle(m0.ravel(), exact_evaluate(G, d, tv_gamma=0.02, tv_beta=1e-9), 1e-11, 3,
+                                 eps_min=1e-13, first_step=0.02)
+    assert res.status == so == "n_iter"
+    assert rel(res.m.cpu().numpy().ravel(), mo) < 1e-8
+    assert abs(res.f - fo) <= 1e-6 * abs(fo)

@@ -322,3 +322,27 @@ def test_awri_oracle_halves_eps_until_the_step_decreases_f():
     assert hist == [{"iteration": 1, "f": 0.25 + 50.0 * 0.025 * 0.5, "eps": 0.025}]
     m, f, status, hist = awri(np.array([1.0, 1.0]), evaluate, 0.1, 1, first_step=0.5, eps_min=0.04)
     assert status == "eps_min" and hist == []
+
+
+# ---------------------------------------------------------------- TV term (Eq. TVAWRI)
+def test_total_variation_pins():
+    """Constant model: TV = n beta, zero gradient.  One planar step of height c across a face
+    of n_face nodes: TV = (n - n_face) beta + n_face sqrt(c^2 + beta^2).  Gradient: central
+    differences on random directions."""
+    shp = (5, 6, 7)
+    n = 5 * 6 * 7
+    tv, g = O.total_variation(np.full(shp, 3.0), 0.1)
+    assert np.isclose(tv, n * 0.1, rtol=1e-14) and np.abs(g).max() == 0.0
+    m = np.zeros(shp)
+    m[:, :, 4:] = 2.0                       # step between x = 3 and x = 4
+    tv, _ = O.total_variation(m, 0.1)
+    n_face = 5 * 6
+    assert np.isclose(tv, (n - n_face) * 0.1 + n_face * np.sqrt(4.0 + 0.01), rtol=1e-14)
+    r = synth.rng(31)
+    m = r.standard_normal(shp)
+    tv, g = O.total_variation(m, 0.3)
+    for _ in range(3):
+        dm = r.standard_normal(shp)
+        eps = 1e-6
+        fd = (O.total_variation(m + eps * dm, 0.3)[0] - O.total_variation(m - eps * dm, 0.3)[0]) / (2 * eps)
+        assert abs(fd - float((g * dm).sum())) <= 1e-7 * abs(fd)
