@@ -137,3 +137,30 @@ def test_awri_product_loop_matches_oracle_loop():
     assert any(h["eps"] < 0.2 for h in ho)           # the case exercises the halving
     assert np.allclose(res.m.numpy(), mo, rtol=1e-12, atol=1e-14)
     assert abs(res.f - fo) <= 1e-12 * abs(fo)
+
+
+def test_objective_chunk_slices_geometry_and_data():
+    """A chunk [b, e) of a group keeps exactly its systems' sources, receiver lists (CSR offsets
+    rebased to 0), data entries and known weights, and takes the given model and wavefields."""
+    from dataclasses import replace
+
+    from paper_2410_18429_gb300.objective import _sub
+    from paper_2410_18429_gb300.wri import GroupSpec
+    rec_off = np.array([0, 3, 5, 9, 10], np.int32)
+    rec_idx = np.arange(10, dtype=np.int32) * 7
+    d = torch.arange(10, dtype=torch.float32).to(torch.complex64)
+    alpha = torch.arange(8, dtype=torch.float64).reshape(4, 2)
+    g = GroupSpec(8, 6, 5, 1, 10.0, 30.0, 2000.0, None, np.array([11, 22, 33, 44], np.int64), rec_off, rec_idx, d,
+                  0.01, None, alpha)
+    m = torch.zeros(5, 6, 8)
+    u = torch.zeros(2, 240, dtype=torch.complex64)
+    s = _sub(g, 1, 3, m, u)
+    assert s.src.tolist() == [22, 33] and s.nsys == 2
+    assert s.rec_off.tolist() == [0, 2, 6] and s.rec_off.dtype == np.int32
+    assert s.rec_idx.tolist() == [21, 28, 35, 42, 49, 56]
+    assert s.d.real.tolist() == [3, 4, 5, 6, 7, 8]
+    assert s.alpha.tolist() == [[2.0, 3.0], [4.0, 5.0]]
+    assert s.m is m and s.u is u and s.u64 is None and (s.nx, s.ny, s.nz, s.lam) == (8, 6, 5, 0.01)
+    s2 = _sub(replace(g, alpha=None), 0, 4, m, u)
+    assert s2.alpha is None and s2.rec_off.tolist() == rec_off.tolist()
+
