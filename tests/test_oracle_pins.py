@@ -101,6 +101,33 @@ def test_free_space_greens_function():
     assert max(errs) < 0.05, errs
 
 
+@pytest.mark.slow
+def test_free_space_greens_function_converges_at_second_order():
+    """Halving h at a fixed absorbing-layer thickness in metres (8 -> 16 points per wavelength)
+    cuts the error against -h^3 exp(i k r)/(4 pi r) at fixed physical points by about 4: the
+    7-point stencil is second order.  A misplaced half-node coefficient or a stretch applied on the
+    wrong side leaves a first-order (or no) decrease and fails the window."""
+    v = 2000.0
+    freq = v / (8 * 20.0)
+    om, k = 2 * np.pi * freq, 2 * np.pi * freq / v
+    offsets_m = [(40, 0, 0), (0, 60, 0), (0, 0, 80), (40, 40, 0), (40, 40, 40), (60, 40, 0), (0, 80, 40)]
+    rms = []
+    for h, nph, npml in ((20.0, 11, 2), (10.0, 21, 4)):
+        g = synth.grid(nph, npml, h)
+        A = O.helmholtz_matrix(g.shape, h, om, synth.to_m(synth.velocity_homogeneous(g, v)), npml, v)
+        c = nph // 2
+        u = spla.splu(A.tocsc()).solve(O.unit_vector(g.n, synth.node_index(g, c, c, c)) * 1.0)
+        e = []
+        for off in offsets_m:
+            di = [int(round(x / h)) for x in off]
+            r = h * np.sqrt(sum(x * x for x in di))
+            ref = -h ** 3 * np.exp(1j * k * r) / (4 * np.pi * r)
+            e.append(abs(u[synth.node_index(g, c + di[0], c + di[1], c + di[2])] - ref) / abs(ref))
+        rms.append(np.sqrt(np.mean(np.square(e))))
+    assert rms[1] < 0.03, rms
+    assert 3.0 <= rms[0] / rms[1] <= 6.0, rms
+
+
 # ---------------------------------------------------------------- exact solves (step a3)
 @pytest.mark.parametrize("source_free", [True, False])
 def test_exact_solvers_agree_with_dense_lstsq(source_free):
