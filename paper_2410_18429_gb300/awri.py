@@ -17,9 +17,14 @@ Readings (the paper states none of these):
   * the evaluation at an accepted m~ is reused as the next iteration's first evaluation (it is
     the same solve at the same model and tolerance);
   * if a step fails with eps already below ``eps_min`` the loop stops (status "eps_min").
+
+The loop's whole state between iterations (model, f, g, eps, the l-BFGS pairs, counters and
+history) is an ``AwriState``; ``save_state`` / ``load_state`` write and read it with
+``torch.save``, and ``awri(..., state=...)`` continues from it exactly as if never interrupted.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 from typing import Callable, List, Optional, Tuple
 
@@ -29,12 +34,13 @@ import torch
 class LBFGS:
     """Limited-memory BFGS inverse-Hessian product by the two-loop recursion."""
 
-    def __init__(self, memory: int = 5):
+    def __init__(self, memory: int = 5, s: Optional[List[torch.Tensor]] = None,
+                 y: Optional[List[torch.Tensor]] = None):
         if memory < 1:
             raise ValueError("memory >= 1")
         self.memory = memory
-        self.s: List[torch.Tensor] = []
-        self.y: List[torch.Tensor] = []
+        self.s: List[torch.Tensor] = [] if s is None else s
+        self.y: List[torch.Tensor] = [] if y is None else y
 
     def update(self, s: torch.Tensor, y: torch.Tensor) -> bool:
         """Store the pair if it satisfies the curvature condition; returns whether it was kept."""
@@ -69,29 +75,68 @@ class LBFGS:
 
 
 @dataclass
+class AwriState:
+    """The outer loop between two iterations: model m with its f and g at tolerance eps, the
+    stored l-BFGS pairs (oldest first), the iterations and evaluations done, and the history."""
+
+    m: torch.Tensor
+    f: float
+    g: torch.Tensor
+    eps: float
+    s: List[torch.Tensor] = field(default_factory=list)
+    y: List[torch.Tensor] = field(default_factory=list)
+    iteration: int = 0
+    evaluations: int = 0
+    history: List[dict] = field(default_factory=list)
+
+
+def save_state(state: AwriState, path: str) -> None:
+    """Write the state with ``torch.save`` (to a temporary file first, then renamed, so an
+    interrupted write leaves the previous checkpoint intact)."""
+    tmp = path + ".tmp"
+    torch.save({"m": state.m, "f": state.f, "g": state.g, "eps": state.eps, "s": state.s, "y": state.y,
+                "iteration": state.iteration, "evaluations": state.evaluations, "history": state.history}, tmp)
+    os.replace(tmp, path)
+
+
+def load_state(path: str, device=None) -> AwriState:
+    """Read a state written by ``save_state``; tensors go to ``device`` (default: where they were)."""
+    d = torch.load(path, map_location=device, weights_only=True)
+    return AwriState(m=d["m"], f=float(d["f"]), g=d["g"], eps=float(d["eps"]), s=list(d["s"]), y=list(d["y"]),
+                     iteration=int(d["iteration"]), evaluations=int(d["evaluations"]), history=list(d["history"]))
+
+
+@dataclass
 class AwriResult:
     m: torch.Tensor
     f: float
     status: str                                    # "n_iter" or "eps_min"
     history: List[dict] = field(default_factory=list)
     evaluations: int = 0
+    state: Optional[AwriState] = None              # to continue the loop (``awri(..., state=...)``)
 
 
-def awri(m0: torch.Tensor, evaluate: Callable[[torch.Tensor, float], Tuple[float, torch.Tensor]],
+def awri(m0: Optional[torch.Tensor], evaluate: Callable[[torch.Tensor, float], Tuple[float, torch.Tensor]],
          eps0: float, n_iter: int, eps_min: float = 1e-12, memory: int = 5, first_step: float = 0.05,
-         model_error: Optional[Callable[[torch.Tensor], float]] = None) -> AwriResult:
+         model_error: Optional[Callable[[torch.Tensor], float]] = None, state: Optional[AwriState] = None,
+         checkpoint: Optional[str] = None) -> AwriResult:
     """Algorithm 2 (gamma = 0).  ``evaluate(m, eps) -> (f, g)`` gives f4 and g4 at m with the
-    systems solved to tolerance eps (e.g. ``make_evaluate``)."""
+    systems solved to tolerance eps (e.g. ``make_evaluate``).
+
+    ``n_iter`` counts all iterations, those of a resumed ``state`` included; with ``state`` the
+    loop continues from it (m0 and eps0 are then not used).  With ``checkpoint`` the state is
+    saved there after every accepted iteration."""
     if not (eps0 > 0 and n_iter >= 0):
         raise ValueError("eps0 > 0 and n_iter >= 0 required")
-    m = m0.detach().clone().to(torch.float64)
-    eps = float(eps0)
-    lb = LBFGS(memory)
-    f, g = evaluate(m, eps)
-    evals = 1
-    hist = []
+    if state is None:
+        m = m0.detach().clone().to(torch.float64)
+        eps = float(eps0)
+        f, g = evaluate(m, eps)
+        state = AwriState(m=m, f=f, g=g, eps=eps, evaluations=1)
+    lb = LBFGS(memory, state.s, state.y)
+    m, f, g, eps, evals = state.m, state.f, state.g, state.eps, state.evaluations
     status = "n_iter"
-    for k in range(n_iter):
+    for k in range(state.iteration, n_iter):
         while True:
             h0 = None
             if not lb.s:
@@ -115,8 +160,12 @@ def awri(m0: torch.Tensor, evaluate: Callable[[torch.Tensor, float], Tuple[float
         rec = {"iteration": k + 1, "f": f, "eps": eps, "evaluations": evals}
         if model_error is not None:
             rec["model_error"] = float(model_error(m))
-        hist.append(rec)
-    return AwriResult(m=m, f=f, status=status, history=hist, evaluations=evals)
+        state.history.append(rec)
+        state.m, state.f, state.g, state.eps, state.iteration, state.evaluations = m, f, g, eps, k + 1, evals
+        if checkpoint is not None:
+            save_state(state, checkpoint)
+    state.m, state.f, state.g, state.eps, state.evaluations = m, f, g, eps, evals
+    return AwriResult(m=m, f=f, status=status, history=state.history, evaluations=evals, state=state)
 
 
 def make_evaluate(groups, opts, max_resident: int = 1 << 30, stats: Optional[dict] = None, tv_gamma: float = 0.0,

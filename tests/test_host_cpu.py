@@ -164,3 +164,36 @@ def test_objective_chunk_slices_geometry_and_data():
     s2 = _sub(replace(g, alpha=None), 0, 4, m, u)
     assert s2.alpha is None and s2.rec_off.tolist() == rec_off.tolist()
 
+
+
+def test_awri_checkpoint_and_resume_continue_exactly(tmp_path):
+    """Eight iterations straight equal three iterations checkpointed to disk, the state loaded
+    back, and the loop continued to eight: the same iterates, objective values, tolerances
+    (halvings included) and evaluation count, bit for bit."""
+    from paper_2410_18429_gb300.awri import awri, load_state
+    r = np.random.Generator(np.random.PCG64(7))
+    n = 10
+    U, _ = np.linalg.qr(r.standard_normal((n, n)))
+    Q = torch.as_tensor(U @ np.diag(np.linspace(1.0, 30.0, n)) @ U.T)
+    m_star = torch.as_tensor(r.uniform(1.0, 2.0, n))
+    c = torch.as_tensor(r.standard_normal(n))
+    calls = []
+
+    def evaluate(m, eps):
+        calls.append(eps)
+        e = m - m_star
+        return float(0.5 * e @ Q @ e), Q @ e + 200.0 * eps * c
+
+    m0 = torch.full((n,), 1.5, dtype=torch.float64)
+    full = awri(m0, evaluate, 0.2, 8, first_step=0.3, eps_min=1e-6)
+    n_full = len(calls)
+    assert any(h["eps"] < 0.2 for h in full.history[3:])     # halvings after the checkpoint too
+    calls.clear()
+    path = str(tmp_path / "awri_state.pt")
+    part = awri(m0, evaluate, 0.2, 3, first_step=0.3, eps_min=1e-6, checkpoint=path)
+    st = load_state(path)
+    assert st.iteration == 3 and len(st.s) == len(part.state.s) and st.eps == part.state.eps
+    rest = awri(None, evaluate, 0.2, 8, first_step=0.3, eps_min=1e-6, state=st)
+    assert len(calls) == n_full and rest.evaluations == full.evaluations
+    assert torch.equal(rest.m, full.m) and rest.f == full.f and rest.status == full.status
+    assert rest.history == full.history
