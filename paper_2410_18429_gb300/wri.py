@@ -8,6 +8,7 @@ raises at import: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import json
 import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
@@ -275,12 +276,49 @@ def gradient_noalloc(groups: Sequence[GroupSpec], dtype: int, alpha, grads, f, s
     return grads, f
 
 
-def autotune(groups: Sequence[GroupSpec], opts: WriSolveOpts, trial_iters: int = 12, workspace=None, stream=None):
+def _tune_key(groups: Sequence[GroupSpec], opts: WriSolveOpts, device) -> str:
+    """What the autotuner's choice depends on: the GPU, the library build (its version string
+    carries the kernel-source hash), the options that shape the solve, and every group's grid,
+    system count, receiver count and mode."""
+    import torch
+    name = torch.cuda.get_device_name(device) if device.type == "cuda" else device.type
+    parts = [name, version(), f"dtype={opts.dtype} refine={opts.max_refine} plain={opts.plain} tile={opts.tile} "
+             f"zsplit={opts.zsplit} l2={opts.l2_promotion}"]
+    for g in groups:
+        parts.append(f"{g.nx}x{g.ny}x{g.nz}+{g.npml} nsys={g.nsys} nnz={len(g.rec_idx)} "
+                     f"{'free' if g.alpha is None else 'known'}")
+    return " | ".join(parts)
+
+
+def _read_tune_cache(path: str) -> dict:
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+        return table if isinstance(table, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def autotune(groups: Sequence[GroupSpec], opts: WriSolveOpts, trial_iters: int = 12, workspace=None, stream=None,
+             cache: Optional[str] = None):
     """wri_autotune: a copy of opts with the fastest (kernel, order) for this batch.
 
-    The groups' wavefields are overwritten by the trial solves (unless the choice is cached)."""
-    m = _Marshal(groups)
+    The groups' wavefields are overwritten by the trial solves (unless the choice is cached).
+    ``cache``: a JSON file that keeps choices across processes (default: the file named by the
+    environment variable WRI_TUNE_CACHE, else none).  A choice stored there for the same GPU,
+    library build, options and batch shape is reused without trial solves; a missing or
+    unreadable file counts as empty, and new choices are written to a temporary file that then
+    replaces it."""
+    path = cache if cache is not None else os.environ.get("WRI_TUNE_CACHE")
     dev = groups[0].u.device
+    key = _tune_key(groups, opts, dev) if path else None
+    if path:
+        hit = _read_tune_cache(path).get(key)
+        if isinstance(hit, dict) and "kernel" in hit and "order" in hit:
+            out = WriSolveOpts.from_buffer_copy(opts)
+            out.kernel, out.order = int(hit["kernel"]), int(hit["order"])
+            return out
+    m = _Marshal(groups)
     nbytes = lib.wri_workspace_size(m.arr, m.n, C.byref(opts))
     if nbytes == 0:
         raise WriError(EINVAL, "wri_workspace_size")
@@ -288,6 +326,13 @@ def autotune(groups: Sequence[GroupSpec], opts: WriSolveOpts, trial_iters: int =
     out = WriSolveOpts.from_buffer_copy(opts)
     _check(lib.wri_autotune(m.arr, m.n, C.byref(out), int(trial_iters), _ptr(ws), ws.numel(), _stream(stream)),
            "wri_autotune")
+    if path:
+        table = _read_tune_cache(path)
+        table[key] = {"kernel": int(out.kernel), "order": int(out.order)}
+        tmp = f"{path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
     return out
 
 

@@ -360,6 +360,24 @@ def test_autotune_choice_solves_like_default_and_is_cached(W):
     assert rel(a2.u.cpu().numpy(), b2.u.cpu().numpy()) < 1e-5
 
 
+def test_autotune_disk_cache_round_trip(W, tmp_path):
+    """The on-disk cache with the real library: the stored choice is the library's, and a second
+    call returns it without trial solves (the wavefields stay untouched)."""
+    import json
+    G = case(nphys=(20, 12, 10), npml=4, nsys=2, seed=6)
+    s = _spec(W, G, 0)
+    base = W.make_opts(tol=0.0, max_iter=20, dtype=0)
+    path = str(tmp_path / "tune.json")
+    first = W.autotune([s], base, trial_iters=4, cache=path)
+    with open(path) as fh:
+        stored = list(json.load(fh).values())
+    assert stored == [{"kernel": first.kernel, "order": first.order}]
+    s.u.fill_(2.0)
+    again = W.autotune([s], base, trial_iters=4, cache=path)
+    assert (again.kernel, again.order) == (first.kernel, first.order)
+    assert float(s.u.real.min()) == 2.0 == float(s.u.real.max())
+
+
 def test_plain_path_matches_fused(W):
     G = case(nphys=(21, 13, 11), npml=4, nsys=2)
     sa, sb = _spec(W, G, 0), _spec(W, G, 0)

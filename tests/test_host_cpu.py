@@ -1,5 +1,7 @@
 """Host-side logic that needs no GPU: the source sharding and gradient sum of the multi-rank
-path (two gloo ranks on CPU), and the chunking of the autograd objective."""
+path (two gloo ranks on CPU), the chunking of the autograd objective, the outer loop's control
+flow and checkpoints, and the on-disk autotune cache."""
+import json
 import os
 import socket
 
@@ -197,3 +199,69 @@ def test_awri_checkpoint_and_resume_continue_exactly(tmp_path):
     assert len(calls) == n_full and rest.evaluations == full.evaluations
     assert torch.equal(rest.m, full.m) and rest.f == full.f and rest.status == full.status
     assert rest.history == full.history
+
+
+def test_autotune_disk_cache(tmp_path, monkeypatch):
+    """The on-disk autotune cache: a miss runs the library's trials and stores the choice, a hit
+    for the same GPU, build, options and batch reuses it without trials, and a change in any of
+    them (or an unreadable file) runs the trials again.  The library is a fake that records its
+    calls (no GPU); the key logic and the file handling are the product's."""
+    from paper_2410_18429_gb300 import wri
+
+    class FakeLib:
+        def __init__(self):
+            self.calls = 0
+            self.ver = b"libwri fake src 000"
+
+        def wri_workspace_size(self, arr, n, opts):
+            return 1024
+
+        def wri_autotune(self, arr, n, opts_ref, trial_iters, ws, nbytes, stream):
+            self.calls += 1
+            opts_ref._obj.kernel, opts_ref._obj.order = 2 + 18, 5
+            return wri.OK
+
+        def wri_version(self):
+            return self.ver
+
+        def wri_strerror(self, code):
+            return b"fake"
+
+    fake = FakeLib()
+    monkeypatch.setattr(wri, "lib", fake)
+    monkeypatch.setattr(wri, "_stream", lambda stream=None: None)
+    monkeypatch.delenv("WRI_TUNE_CACHE", raising=False)
+
+    def group(nsys):
+        n = 6 * 5 * 4
+        return wri.GroupSpec(6, 5, 4, 1, 10.0, 30.0, 2000.0, torch.zeros(4, 5, 6), np.arange(nsys, dtype=np.int64),
+                             np.arange(nsys + 1, dtype=np.int32), np.arange(nsys, dtype=np.int32) + 50,
+                             torch.zeros(nsys, dtype=torch.complex64), 0.01, torch.zeros(nsys, n, dtype=torch.complex64))
+
+    opts = wri.make_opts(tol=1e-3, max_iter=100)
+    path = str(tmp_path / "tune.json")
+    out = wri.autotune([group(3)], opts, cache=path)
+    assert (fake.calls, out.kernel, out.order) == (1, 20, 5) and (opts.kernel, opts.order) == (0, 0)
+    out = wri.autotune([group(3)], opts, cache=path)                     # hit: no trials
+    assert (fake.calls, out.kernel, out.order) == (1, 20, 5)
+    monkeypatch.setenv("WRI_TUNE_CACHE", path)                           # the same file through the variable
+    assert wri.autotune([group(3)], opts).kernel == 20 and fake.calls == 1
+    wri.autotune([group(4)], opts)                                       # another batch shape
+    assert fake.calls == 2
+    wri.autotune([group(3)], wri.make_opts(tol=1e-3, max_iter=100, dtype=wri.C128))   # other options
+    assert fake.calls == 3
+    fake.ver = b"libwri fake src 111"                                    # a rebuilt library
+    wri.autotune([group(3)], opts)
+    assert fake.calls == 4
+    with open(path) as fh:
+        assert len(json.load(fh)) == 4
+    with open(path, "w") as fh:
+        fh.write("{not json")
+    wri.autotune([group(3)], opts)                                       # unreadable file: trials, rewritten
+    assert fake.calls == 5
+    with open(path) as fh:
+        assert len(json.load(fh)) == 1
+    monkeypatch.delenv("WRI_TUNE_CACHE")
+    wri.autotune([group(3)], opts)                                       # no cache: always trials
+    wri.autotune([group(3)], opts)
+    assert fake.calls == 7
