@@ -153,3 +153,16 @@ def test_tv_rejects_invalid_arguments(W):
     assert W.lib.wri_tv(C.byref(g), 0x1000, 0.1, 1.0, None, None, None) == W.EINVAL        # no output
     g2 = W.WriGrid(2, 18, 16, 0, 10.0, 60.0, 1e-3, 2000.0)
     assert W.lib.wri_tv(C.byref(g2), 0x1000, 0.1, 1.0, 0x2000, None, None) == W.EINVAL
+
+
+def test_empty_batches_are_rejected(W):
+    """A group without systems, a call without groups and a NULL group array are argument errors
+    (nsys >= 1 and at least one group), caught before any device work."""
+    o = W.make_opts()
+    empty = _spec(W, src=np.zeros(0, np.int64), rec_off=np.array([0], np.int32), rec_idx=np.zeros(0, np.int32))
+    assert W.workspace_size([empty], o) == 0
+    assert W.workspace_size([_spec(W), empty], o) == 0
+    m = W._Marshal([_spec(W)])
+    assert W.lib.wri_workspace_size(m.arr, 0, C.byref(o)) == 0
+    assert W.lib.wri_solve_batch(m.arr, 0, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 30, None) == W.EINVAL
+    assert W.lib.wri_solve_batch(None, 1, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 30, None) == W.EINVAL
