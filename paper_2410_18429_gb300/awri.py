@@ -128,6 +128,8 @@ def awri(m0: Optional[torch.Tensor], evaluate: Callable[[torch.Tensor, float], T
     saved there after every accepted iteration."""
     if not (eps0 > 0 and n_iter >= 0):
         raise ValueError("eps0 > 0 and n_iter >= 0 required")
+    if state is None and m0 is None:
+        raise ValueError("a starting model m0 or a state to resume from is required")
     if state is None:
         m = m0.detach().clone().to(torch.float64)
         eps = float(eps0)

@@ -199,6 +199,8 @@ def test_awri_checkpoint_and_resume_continue_exactly(tmp_path):
     assert len(calls) == n_full and rest.evaluations == full.evaluations
     assert torch.equal(rest.m, full.m) and rest.f == full.f and rest.status == full.status
     assert rest.history == full.history
+    with pytest.raises(ValueError):
+        awri(None, evaluate, 0.2, 8)
 
 
 def test_autotune_disk_cache(tmp_path, monkeypatch):
