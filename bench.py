@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--zsplit", type=int, default=0, help="z-chunks per tile column (0 = library choice)")
     p.add_argument("--promo", type=int, default=0, help="TMA L2 promotion: 0 auto, 1 none, 2 64B, 3 128B, 4 256B")
     p.add_argument("--cpu-iters", type=int, default=8, help="oracle CGLS iterations per CPU sample")
+    p.add_argument("--group-sweep", default="",
+                   help="comma-separated systems per call (e.g. 1,2,4,8,16,32): instead of the bench line, time "
+                        "one CGLS iteration of that many systems of the 148^3 group in one batched call and "
+                        "print one JSON line for each (the grouping sweep of Eq. Mmatrix2)")
     return p.parse_args()
 
 
@@ -208,12 +212,79 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- grouping sweep
+def run_group_sweep(args):
+    """Grouping (Eq. Mmatrix2): one CGLS iteration of n_b systems of the largest grid advanced by
+    one batched call, for every n_b of ``--group-sweep`` (the default TMA configuration and
+    order unless ``--kernel`` / ``--order`` say otherwise; no autotuning, so every n_b runs the
+    same kernel).  The per-iteration time is the difference of two solves of 20 and 80
+    iterations (tol = 0, CUDA events on the launching stream, best of two each), which removes
+    the set-up; algorithmic bytes are those of the bench line."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2410_18429_gb300 import wri
+    from paper_2410_18429_gb300.problem import to_device
+
+    sizes = [int(x) for x in args.group_sweep.split(",") if x.strip()]
+    groups = workload(args)
+    g0 = max(groups, key=lambda g: g.spec.n)
+    if not sizes or min(sizes) < 1 or max(sizes) > g0.nsys:
+        raise SystemExit(f"--group-sweep sizes must lie in 1..{g0.nsys}")
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        peak = 6800.0
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    n = g0.spec.n
+    for nb in sizes:
+        sub = synth.Group(g0.spec, g0.freq, g0.v, g0.src[:nb], g0.rec_off[:nb + 1] - g0.rec_off[0],
+                          g0.rec_idx[g0.rec_off[0]:g0.rec_off[nb]], g0.lam, g0.v_max, g0.pml_R, g0.alpha[:nb],
+                          g0.d[g0.rec_off[0]:g0.rec_off[nb]])
+        spec = to_device(sub, wri.C64, dev)
+        base = wri.make_opts(tol=0.0, max_iter=1, dtype=wri.C64, poll_every=K_POLL, kernel=args.kernel,
+                             order=args.order, zsplit=args.zsplit, l2_promotion=args.promo)
+        work = torch.empty(wri.workspace_size([spec], base), dtype=torch.uint8, device=dev)
+
+        def timed(iters):
+            o = wri.WriSolveOpts.from_buffer_copy(base)
+            o.max_iter = iters
+            ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            wri.solve([spec], o, workspace=work)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) * 1e-3
+
+        timed(20)
+        ta = min(timed(20) for _ in range(2))
+        tb = min(timed(80) for _ in range(2))
+        t_iter = (tb - ta) / 60.0
+        alg = n * (BYTES_PER_NODE_SYS * nb + MODEL_BYTES)
+        print(json.dumps({"group_sweep": nb, "grid": f"{g0.spec.nx}x{g0.spec.ny}x{g0.spec.nz}",
+                          "ms_per_iter": t_iter * 1e3, "us_per_system_iter": t_iter / nb * 1e6,
+                          "gpt_iter_s": nb * n / t_iter / 1e9, "hbm_gbs": alg / t_iter / 1e9,
+                          "frac_of_measured_hbm": alg / t_iter / 1e9 / peak,
+                          "cg_vector_mb": 6 * nb * n * 8 / 1e6, "kernel": int(base.kernel), "order": int(base.order),
+                          "device": torch.cuda.get_device_name(dev)}), flush=True)
+        del spec, work
+        torch.cuda.empty_cache()
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.group_sweep:
+        run_group_sweep(args)
         return
     import numpy as np
     import torch
