@@ -25,3 +25,11 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_group_sweep_rejects_sizes_outside_the_group():
+    """The grouping sweep checks its sizes against the group's systems before any device work."""
+    for bad in ("0", "1,129", ","):
+        out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--group-sweep", bad],
+                             capture_output=True, text=True, timeout=600, cwd=ROOT)
+        assert out.returncode != 0 and "--group-sweep sizes must lie in 1..128" in out.stderr, (bad, out.stderr)
