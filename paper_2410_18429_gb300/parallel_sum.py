@@ -7,13 +7,22 @@ from __future__ import annotations
 
 
 def allreduce_gradient(grads, f, group=None):
-    """In-place all-reduce (sum) of the gradient tensors and the objective."""
+    """In-place all-reduce (sum) of the gradient tensors and the objective.
+
+    All of them (float64, one device) travel in one flat buffer, so the exchange is a single
+    collective however many frequency groups there are."""
+    import torch
     import torch.distributed as dist
     if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
         return grads, f
-    for g in grads:
-        dist.all_reduce(g, op=dist.ReduceOp.SUM, group=group)
-    dist.all_reduce(f, op=dist.ReduceOp.SUM, group=group)
+    parts = list(grads) + [f]
+    flat = torch.cat([t.reshape(-1) for t in parts])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    off = 0
+    for t in parts:
+        k = t.numel()
+        t.copy_(flat[off:off + k].view_as(t))
+        off += k
     return grads, f
 
 

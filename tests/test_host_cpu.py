@@ -37,11 +37,15 @@ def _rank_main(rank, world, port, out_dir):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     # each rank owns a shard of 10 systems; its gradient is the sum of per-system terms
     b, e = shard(10, rank, world)
+    # two frequency groups on grids of different shapes
     per_system = [torch.arange(12, dtype=torch.float64).reshape(2, 2, 3) * (s + 1) for s in range(10)]
-    g = [sum(per_system[b:e], torch.zeros(2, 2, 3, dtype=torch.float64))]
+    per_system_b = [torch.arange(20, dtype=torch.float64).reshape(4, 5) - s for s in range(10)]
+    g = [sum(per_system[b:e], torch.zeros(2, 2, 3, dtype=torch.float64)),
+         sum(per_system_b[b:e], torch.zeros(4, 5, dtype=torch.float64))]
     f = torch.tensor([float(sum(s + 1 for s in range(b, e)))], dtype=torch.float64)
-    allreduce_gradient(g, f)
-    torch.save({"g": g[0], "f": f}, os.path.join(out_dir, f"r{rank}.pt"))
+    out = allreduce_gradient(g, f)
+    assert out[0] is g and out[1] is f                       # summed in place
+    torch.save({"g": g[0], "g_b": g[1], "f": f}, os.path.join(out_dir, f"r{rank}.pt"))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -52,9 +56,10 @@ def test_gradient_allreduce_two_gloo_ranks(tmp_path):
     port = _free_port()
     mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
     want_g = torch.arange(12, dtype=torch.float64).reshape(2, 2, 3) * sum(range(1, 11))
+    want_b = torch.arange(20, dtype=torch.float64).reshape(4, 5) * 10 - sum(range(10))
     for r in range(2):
         got = torch.load(os.path.join(tmp_path, f"r{r}.pt"))
-        assert torch.equal(got["g"], want_g)
+        assert torch.equal(got["g"], want_g) and torch.equal(got["g_b"], want_b)
         assert got["f"].item() == 55.0
 
 
