@@ -149,16 +149,59 @@ class GroupSpec:
         return WriGrid(self.nx, self.ny, self.nz, self.npml, self.h, self.omega, self.pml_R, self.v_max)
 
 
-class _Marshal:
-    """Builds the C array of wri_group and keeps the host geometry alive."""
+def _device_tensor(t, what: str, dev=None, dtype=None, min_numel: Optional[int] = None):
+    """Check a tensor handed to the library as a device pointer: on a CUDA device (the same as
+    the call's other tensors), contiguous, of the dtype the call's arithmetic reads and large
+    enough.  A host tensor or a short buffer would otherwise reach the kernels as a bad device
+    address.  Objects that are not torch tensors (raw pointer holders) are passed through: the
+    library checks what it can.  Returns the device seen so far."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        return dev
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{what} must be {dtype} for this call (it is {t.dtype})")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{what} holds {t.numel()} elements; {min_numel} are needed")
+    if t.device.type != "cuda":
+        raise ValueError(f"{what} must be a CUDA tensor (it is on {t.device})")
+    if dev is not None and t.device != dev:
+        raise ValueError(f"{what} is on {t.device}, the call's other tensors on {dev}")
+    return t.device
 
-    def __init__(self, groups: Sequence[GroupSpec]):
+
+def _dtypes(dtype):
+    """(real, complex) torch dtypes of the arithmetic type ``dtype`` (None: not known here)."""
+    import torch
+    if dtype == C64:
+        return torch.float32, torch.complex64
+    if dtype == C128:
+        return torch.float64, torch.complex128
+    return None, None
+
+
+class _Marshal:
+    """Builds the C array of wri_group and keeps the host geometry alive.  With the call's
+    arithmetic type ``dtype`` the groups' tensors are checked against it (``_device_tensor``)."""
+
+    def __init__(self, groups: Sequence[GroupSpec], dtype: Optional[int] = None):
+        import torch
         self.keep = []
         arr = (WriGroup * len(groups))()
+        real, cplx = _dtypes(dtype)
+        dev = None
         for i, g in enumerate(groups):
             src = np.ascontiguousarray(g.src, dtype=np.int64)
             off = np.ascontiguousarray(g.rec_off, dtype=np.int32)
             rec = np.ascontiguousarray(g.rec_idx, dtype=np.int32)
+            nsys, n = len(src), g.nx * g.ny * g.nz
+            nnz = int(off[-1]) if len(off) else 0
+            dev = _device_tensor(g.m, f"group {i}: m", dev, real, n)
+            dev = _device_tensor(g.d, f"group {i}: d", dev, cplx, nnz)
+            dev = _device_tensor(g.u, f"group {i}: u", dev, cplx, nsys * n)
+            dev = _device_tensor(g.alpha, f"group {i}: alpha", dev, torch.float64, 2 * nsys)
+            dev = _device_tensor(g.u64, f"group {i}: u64", dev, torch.complex128, nsys * n)
             if len(rec) == 0:
                 rec = np.zeros(1, dtype=np.int32)
             self.keep += [src, off, rec]
@@ -166,6 +209,7 @@ class _Marshal:
                               _ptr(g.d), _ptr(g.alpha), float(g.lam), _ptr(g.u), _ptr(g.u64))
         self.arr = arr
         self.n = len(groups)
+        self.device = dev
 
 
 KERNEL_AUTO, KERNEL_MARCH = 0, 1
@@ -184,7 +228,7 @@ def make_opts(tol=1e-6, max_iter=10000, dtype=C64, warm_start=False, max_refine=
 
 
 def workspace_size(groups: Sequence[GroupSpec], opts: WriSolveOpts) -> int:
-    m = _Marshal(groups)
+    m = _Marshal(groups, int(opts.dtype))
     return int(lib.wri_workspace_size(m.arr, m.n, C.byref(opts)))
 
 
@@ -196,6 +240,8 @@ def aux_workspace_size(groups: Sequence[GroupSpec]) -> int:
 def _workspace(nbytes: int, device, workspace=None):
     import torch
     if workspace is not None and workspace.numel() >= nbytes:
+        _device_tensor(workspace, "workspace", device if isinstance(device, torch.device) and
+                       device.type == "cuda" else None)
         return workspace
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
@@ -206,8 +252,12 @@ def apply_A(g: GroupSpec, x, adjoint: bool = False, out=None, stream=None):
     dtype = C128 if x.dtype == torch.complex128 else C64
     y = torch.empty_like(x) if out is None else out
     grid = g.grid()
-    f = lib.wri_apply_AH if adjoint else lib.wri_apply_A
     nsys = x.shape[0] if x.dim() > 1 else 1
+    real, cplx = _dtypes(dtype)
+    dev = _device_tensor(x, "x", None, cplx, nsys * g.n)
+    dev = _device_tensor(y, "out", dev, cplx, nsys * g.n)
+    _device_tensor(g.m, "m", dev, real, g.n)
+    f = lib.wri_apply_AH if adjoint else lib.wri_apply_A
     _check(f(C.byref(grid), dtype, _ptr(g.m), nsys, _ptr(x), _ptr(y), _stream(stream)), "wri_apply_A")
     return y
 
@@ -215,7 +265,7 @@ def apply_A(g: GroupSpec, x, adjoint: bool = False, out=None, stream=None):
 def solve(groups: Sequence[GroupSpec], opts: WriSolveOpts, workspace=None, stream=None):
     """Solve every system; returns (iters int32, relres float64, status int32) CUDA tensors."""
     import torch
-    m = _Marshal(groups)
+    m = _Marshal(groups, int(opts.dtype))
     dev = groups[0].u.device
     nsys = sum(g.nsys for g in groups)
     nbytes = lib.wri_workspace_size(m.arr, m.n, C.byref(opts))
@@ -233,7 +283,7 @@ def solve(groups: Sequence[GroupSpec], opts: WriSolveOpts, workspace=None, strea
 def source_estimate(groups: Sequence[GroupSpec], dtype: int, workspace=None, stream=None):
     """a_i = (A u_i)[src_i] for every system; returns complex128 CUDA tensor [sum nsys]."""
     import torch
-    m = _Marshal(groups)
+    m = _Marshal(groups, dtype)
     dev = groups[0].u.device
     nsys = sum(g.nsys for g in groups)
     ws = _workspace(lib.wri_aux_workspace_size(m.arr, m.n), dev, workspace)
@@ -243,12 +293,23 @@ def source_estimate(groups: Sequence[GroupSpec], dtype: int, workspace=None, str
     return torch.view_as_complex(out)
 
 
+def _check_outputs(groups, a, grads, f, dev):
+    """The weights read and the gradient and objective buffers written by a gradient call."""
+    import torch
+    if len(grads) != len(groups):
+        raise ValueError(f"{len(grads)} gradient buffers for {len(groups)} groups")
+    dev = _device_tensor(a, "alpha", dev, torch.float64, 2 * sum(g.nsys for g in groups))
+    for i, (g, t) in enumerate(zip(groups, grads)):
+        dev = _device_tensor(t, f"gradient {i}", dev, torch.float64, g.n)
+    _device_tensor(f, "f", dev, torch.float64, 1)
+
+
 def gradient(groups: Sequence[GroupSpec], dtype: int, alpha, grads=None, f=None, workspace=None, stream=None):
     """Accumulate g and f (Eqs. VarG2 / VarObj2).  alpha: complex128 [sum nsys].
 
     Returns (list of float64 gradient tensors shaped like each group's m, f tensor [1])."""
     import torch
-    m = _Marshal(groups)
+    m = _Marshal(groups, dtype)
     dev = groups[0].u.device
     ws = _workspace(lib.wri_aux_workspace_size(m.arr, m.n), dev, workspace)
     if grads is None:
@@ -256,6 +317,7 @@ def gradient(groups: Sequence[GroupSpec], dtype: int, alpha, grads=None, f=None,
     if f is None:
         f = torch.zeros(1, dtype=torch.float64, device=dev)
     a = torch.view_as_real(alpha.to(torch.complex128).contiguous())
+    _check_outputs(groups, a, grads, f, m.device)
     gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
     _check(lib.wri_gradient(m.arr, m.n, dtype, _ptr(a), gp, _ptr(f), _ptr(ws), ws.numel(), _stream(stream)),
            "wri_gradient")
@@ -268,8 +330,9 @@ def gradient_noalloc(groups: Sequence[GroupSpec], dtype: int, alpha, grads, f, s
     For callers that cannot allocate device memory; grads and f are caller-owned
     tensors that are accumulated into."""
     import torch
-    m = _Marshal(groups)
+    m = _Marshal(groups, dtype)
     a = torch.view_as_real(alpha.to(torch.complex128).contiguous())
+    _check_outputs(groups, a, grads, f, m.device)
     gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
     _check(lib.wri_gradient_noalloc(m.arr, m.n, dtype, _ptr(a), gp, _ptr(f), _stream(stream)),
            "wri_gradient_noalloc")
@@ -318,7 +381,7 @@ def autotune(groups: Sequence[GroupSpec], opts: WriSolveOpts, trial_iters: int =
             out = WriSolveOpts.from_buffer_copy(opts)
             out.kernel, out.order = int(hit["kernel"]), int(hit["order"])
             return out
-    m = _Marshal(groups)
+    m = _Marshal(groups, int(opts.dtype))
     nbytes = lib.wri_workspace_size(m.arr, m.n, C.byref(opts))
     if nbytes == 0:
         raise WriError(EINVAL, "wri_workspace_size")
@@ -344,6 +407,9 @@ def tv(g: GroupSpec, m, beta: float, gamma: float = 1.0, out=None, grad=None, st
     mm = m.detach().to(torch.float64).contiguous()
     if out is None:
         out = torch.zeros(1, dtype=torch.float64, device=mm.device)
+    dev = _device_tensor(mm, "m", None, torch.float64, g.n)
+    dev = _device_tensor(out, "tv", dev, torch.float64, 1)
+    _device_tensor(grad, "grad", dev, torch.float64, g.n)
     grid = g.grid()
     _check(lib.wri_tv(C.byref(grid), _ptr(mm), float(beta), float(gamma), _ptr(out), _ptr(grad), _stream(stream)),
            "wri_tv")

@@ -166,3 +166,43 @@ def test_empty_batches_are_rejected(W):
     assert W.lib.wri_workspace_size(m.arr, 0, C.byref(o)) == 0
     assert W.lib.wri_solve_batch(m.arr, 0, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 30, None) == W.EINVAL
     assert W.lib.wri_solve_batch(None, 1, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 30, None) == W.EINVAL
+
+
+def test_binding_rejects_host_and_mismatched_tensors(W, monkeypatch):
+    """Tensors handed to the library as device pointers are checked before any library call:
+    contiguous, of the call's dtype, large enough, and on a CUDA device.  A host tensor would
+    otherwise reach the kernels as a bad device address."""
+    import torch
+
+    class NoLib:
+        def __getattr__(self, name):
+            raise AssertionError(f"{name} called although the arguments are invalid")
+
+    n = 20 * 18 * 16
+    with pytest.raises(ValueError, match="contiguous"):
+        W._device_tensor(torch.zeros(4, 4).t(), "x")
+    with pytest.raises(ValueError, match="float64"):
+        W._device_tensor(torch.zeros(4, dtype=torch.float32), "m", None, torch.float64, 4)
+    with pytest.raises(ValueError, match="elements"):
+        W._device_tensor(torch.zeros(3, dtype=torch.float64), "m", None, torch.float64, 4)
+    with pytest.raises(ValueError, match="CUDA"):
+        W._device_tensor(torch.zeros(4, dtype=torch.float64), "m", None, torch.float64, 4)
+    assert W._device_tensor(_FakeTensor(), "m", "dev0") == "dev0"          # pointer holders pass through
+
+    host = _spec(W, m=torch.zeros(16, 18, 20), d=torch.zeros(5, dtype=torch.complex64),
+                 u=torch.zeros(2, n, dtype=torch.complex64))
+    with pytest.raises(ValueError, match="group 0: m must be a CUDA tensor"):
+        W._Marshal([host], W.C64)
+    with pytest.raises(ValueError, match="group 0: m must be torch.float64"):
+        W._Marshal([host], W.C128)
+    with pytest.raises(ValueError, match="group 0: u holds"):
+        W._Marshal([_spec(W, u=torch.zeros(1, n, dtype=torch.complex64))], W.C64)
+    monkeypatch.setattr(W, "lib", NoLib())
+    with pytest.raises(ValueError):
+        W.solve([host], W.make_opts())
+    with pytest.raises(ValueError):
+        W.apply_A(_spec(W, m=torch.zeros(16, 18, 20)), torch.zeros(2, n, dtype=torch.complex64))
+    with pytest.raises(ValueError):
+        W.tv(_spec(W), torch.zeros(16, 18, 20, dtype=torch.float64), 0.1)
+    with pytest.raises(ValueError, match="gradient buffers"):
+        W.gradient_noalloc([_spec(W)], W.C64, torch.zeros(2, dtype=torch.complex128), [], torch.zeros(1))

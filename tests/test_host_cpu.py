@@ -239,11 +239,17 @@ def test_autotune_disk_cache(tmp_path, monkeypatch):
     monkeypatch.setattr(wri, "_stream", lambda stream=None: None)
     monkeypatch.delenv("WRI_TUNE_CACHE", raising=False)
 
+    class Ptr:
+        """A device-pointer holder (not a tensor): the fake library never dereferences it."""
+        device = torch.device("cpu")
+
+        def data_ptr(self):
+            return 0x1000
+
     def group(nsys):
-        n = 6 * 5 * 4
-        return wri.GroupSpec(6, 5, 4, 1, 10.0, 30.0, 2000.0, torch.zeros(4, 5, 6), np.arange(nsys, dtype=np.int64),
+        return wri.GroupSpec(6, 5, 4, 1, 10.0, 30.0, 2000.0, Ptr(), np.arange(nsys, dtype=np.int64),
                              np.arange(nsys + 1, dtype=np.int32), np.arange(nsys, dtype=np.int32) + 50,
-                             torch.zeros(nsys, dtype=torch.complex64), 0.01, torch.zeros(nsys, n, dtype=torch.complex64))
+                             Ptr(), 0.01, Ptr())
 
     opts = wri.make_opts(tol=1e-3, max_iter=100)
     path = str(tmp_path / "tune.json")
