@@ -33,3 +33,33 @@ def test_group_sweep_rejects_sizes_outside_the_group():
         out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--group-sweep", bad],
                              capture_output=True, text=True, timeout=600, cwd=ROOT)
         assert out.returncode != 0 and "--group-sweep sizes must lie in 1..128" in out.stderr, (bad, out.stderr)
+
+
+def test_clock_sampler_parses_speeds_and_throttle_reasons(tmp_path):
+    """The clock record of the timed region: median SM clock, the maximum, and every throttle
+    reason seen Active in any sample (malformed lines are skipped, the sample file removed)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self):
+            return 0
+
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as fh:
+        fh.write("2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "1995, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "garbage line\n"
+                 "[N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "2040, 2070, 1200.0, 0x40, Not Active, Active, Not Active, Not Active\n")
+    c.p, c.out = Done(), open(os.devnull, "w")
+    rec = c.stop()
+    assert rec["sm_mhz"] == 2040.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert not os.path.exists(c.path)
+    c2 = bench.Clocks(0)
+    assert c2.stop()["reasons"] == ["nvidia-smi unavailable"]       # sampler never started
