@@ -125,6 +125,13 @@ typedef struct {
                           4 / 5 / 6 = blocks of 4 / 8 / 16 systems, tiles in order */
   int32_t l2_promotion; /* TMA copies: L2 fill size on a miss, 0 = automatic, 1 = none,
                            2 = 64 B, 3 = 128 B, 4 = 256 B */
+  int32_t wait_limit_us; /* TMA phases: time limit of every wait of the copy pipelines, in
+                            microseconds (0 = 2 s).  A wait that runs out stops the solve:
+                            wri_solve_batch returns WRI_ECUDA and the context stays usable. */
+  int32_t test_withhold; /* test hook of the bounded waits, 0 = off.  k > 0: in the warp-specialised
+                            TMA phases the copy warp of block 0 never issues its (k-1)-th plane
+                            fill, so the wait for it runs out after wait_limit_us.  Nothing
+                            faults or hangs; the call returns WRI_ECUDA. */
 } wri_solve_opts;
 
 /* y = A x (wri_apply_A) or y = A^H x (wri_apply_AH) for `nsys` vectors that share the
@@ -194,17 +201,18 @@ WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype
                                  double* const* grad, double* f, wri_stream_t stream);
 
 /* Autotuner of the batched solve (an interface outside the paper, which prescribes no
- * kernel configuration).  For a complex64 batch without refinement it times `trial_iters`
- * CGLS iterations (>= 2) of every candidate pair (TMA configuration 8, 9, 12, 13, 17 or 18 x
- * work-item order 2, 5 or 6) on the caller's own batch, on `stream`, and writes the fastest
- * into opts->kernel and opts->order (other fields unchanged).  Candidates whose workspace
- * exceeds ws_bytes are skipped.
+ * kernel configuration).  For a complex64 batch it times `trial_iters` CGLS iterations (>= 2)
+ * of every candidate pair (TMA configuration 8, 9, 12, 13, 17 or 18 x work-item order 2, 5 or 6)
+ * on the caller's own batch, on `stream`, and writes the fastest into opts->kernel and
+ * opts->order (other fields unchanged).  With refinement (max_refine > 0) the candidates are
+ * the warp-specialised configurations (9, 12, 13, 17, 18), which run its inner solves, and the
+ * trials are plain CGLS solves.  Candidates whose workspace exceeds ws_bytes are skipped.
  *   - groups[g].u is used as the iterate of the trial solves: its contents are overwritten.
  *   - The choice is cached for the process, keyed by the device, the grids, the system counts
  *     and the receiver counts: a repeated call for the same batch shape returns the cached
  *     choice without timing anything (and without touching u).
- *   - Batches the TMA phases cannot take (complex128, refinement, the unfused baseline, an x
- *     extent that is not a multiple of 4) keep opts unchanged and return WRI_OK.
+ *   - Batches the TMA phases cannot take (complex128, the unfused baseline, an x extent that is
+ *     not a multiple of 4) keep opts unchanged and return WRI_OK.
  *   - Synchronises `stream` (it reads event timings on the host). */
 WRI_API int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int trial_iters,
                          void* workspace, size_t ws_bytes, wri_stream_t stream);

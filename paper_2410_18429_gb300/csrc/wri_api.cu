@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -156,6 +157,7 @@ struct Plan {
   size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][2], v_s[WRI_MAXG], v_t1[WRI_MAXG];
   size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG], v_q64[WRI_MAXG], v_g32[WRI_MAXG], v_rmap[WRI_MAXG];
   size_t off_ztab[WRI_MAXG];
+  size_t off_rmask[WRI_MAXG], off_rcol[WRI_MAXG], rmask_bytes[WRI_MAXG], rcol_bytes[WRI_MAXG];
   std::vector<int> rec_base;  // first receiver entry of every group
 };
 
@@ -241,6 +243,15 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
     P.off_ztab[gi] = off;
     off += align_up(sizeof(float) * 2 * 2 * 3 * (size_t)groups[gi].grid.nz);
   }
+  for (int gi = 0; gi < ngroups; ++gi) {  // receiver bitmaps (one bit per node and system)
+    const GroupDev& G = P.g[gi];
+    P.rcol_bytes[gi] = 4 * (size_t)G.nsys * G.ny * G.tiles_x;
+    P.rmask_bytes[gi] = P.rcol_bytes[gi] * (size_t)G.nz;
+    P.off_rcol[gi] = off;
+    off += align_up(P.rcol_bytes[gi]);
+    P.off_rmask[gi] = off;
+    off += align_up(P.rmask_bytes[gi]);
+  }
   for (int gi = 0; gi < ngroups; ++gi) {
     const size_t vb = align_up((size_t)P.vbytes * (size_t)P.g[gi].nsys * (size_t)P.g[gi].n);
     P.v_r1[gi][0] = off; off += vb;
@@ -271,6 +282,7 @@ int validate_opts(const wri_solve_opts* o) {
   if (o->kernel < 0 || o->kernel > 1 + tma_config_count()) return WRI_EINVAL;
   if (o->order < 0 || o->order > 6) return WRI_EINVAL;
   if (o->l2_promotion < 0 || o->l2_promotion > 4) return WRI_EINVAL;
+  if (o->wait_limit_us < 0 || o->test_withhold < 0) return WRI_EINVAL;
   if (o->max_refine > 0) {
     if (o->dtype != WRI_C64) return WRI_ENOTSUP;
     if (!(o->refine_tol >= 0) || !(o->inner_tol > 0 && o->inner_tol < 1)) return WRI_EINVAL;
@@ -307,18 +319,43 @@ void build_sys(const wri_group* groups, int ngroups, const Plan& P, std::vector<
   if (rec.empty()) rec.push_back(0);
 }
 
+// Per-device state shared by every call on that device: the stream graphs are captured on and
+// the cache of instantiated CG-iteration graphs.  Both are guarded by g_mu; a cached graph is
+// reference-counted, so evicting it while another thread still launches it is safe.
 struct DevCtx {
   cudaStream_t cap = nullptr;
-  int* pinned = nullptr;
-  double* pinned_d = nullptr;
   struct Entry {
     std::vector<unsigned char> key;
-    cudaGraphExec_t exec = nullptr;
+    std::shared_ptr<CUgraphExec_st> exec;
+    bool device_loop = false;  // the graph loops on the device (conditional WHILE node)
   };
   std::vector<Entry> graphs;
 };
 std::mutex g_mu;
 DevCtx g_ctx[64];
+
+// Pinned host words through which a call reads its own device counters (systems remaining, the
+// copy-wait error flag, loop bodies run) and the unfused path its scalars: one block per host
+// thread and device, so concurrent calls from different threads never share it.  A call runs
+// on one host thread from start to end.
+struct PollSlots {
+  int* p[64] = {};
+  ~PollSlots() {
+    for (int* q : p)
+      if (q) cudaFreeHost(q);
+  }
+};
+thread_local PollSlots tl_poll;
+
+int* poll_slot() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!tl_poll.p[dev] && cudaHostAlloc((void**)&tl_poll.p[dev], 64, cudaHostAllocDefault) != cudaSuccess) {
+    tl_poll.p[dev] = nullptr;
+    return nullptr;
+  }
+  return tl_poll.p[dev];
+}
 struct Tuned {
   std::vector<long long> key;  // device, groups, then per group nx, ny, nz, nsys, receivers
   int kernel, order;
@@ -329,10 +366,10 @@ DevCtx* ctx() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   DevCtx* c = &g_ctx[dev];
-  if (!c->cap) {
-    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    if (cudaHostAlloc((void**)&c->pinned, 64, cudaHostAllocDefault) != cudaSuccess) return nullptr;
-    c->pinned_d = (double*)(c->pinned + 4);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap = nullptr;
+    return nullptr;
   }
   return c;
 }
@@ -384,9 +421,21 @@ Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_
     G.q64 = P.ir ? ws + P.v_q64[gi] : nullptr;
     G.gvec = (P.ir && inner_view) ? ws + P.v_g32[gi] : nullptr;
     G.ztab = (const float2*)(ws + P.off_ztab[gi]);
+    G.rmask = (const uint32_t*)(ws + P.off_rmask[gi]);
+    G.rcol = (const uint32_t*)(ws + P.off_rcol[gi]);
     b.g[gi] = G;
   }
   return b;
+}
+
+// Receiver bitmaps of every group (the normal-residual norms leave receiver nodes to the finalizer)
+int setup_rmask(const Plan& P, const Batch& b, char* ws, cudaStream_t st) {
+  for (int gi = 0; gi < P.ngroups; ++gi) {
+    WRI_CK(cudaMemsetAsync(ws + P.off_rcol[gi], 0, P.rcol_bytes[gi], st));
+    WRI_CK(cudaMemsetAsync(ws + P.off_rmask[gi], 0, P.rmask_bytes[gi], st));
+  }
+  WRI_CK(launch_rmask(b, P.nsys_total, st));
+  return WRI_OK;
 }
 
 int poll_default(const Plan& P) {
@@ -444,10 +493,12 @@ bool encode_model(CUtensorMap* m, const void* base, const GroupDev& G, int by, i
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool build_tma(const Batch& b, const Plan& P, int* err, int promo, TmaSet& T) {
+bool build_tma(const Batch& b, const Plan& P, int* err, int promo, const wri_solve_opts* o, TmaSet& T) {
   if (!encode_fn()) return false;
   std::memset(&T, 0, sizeof(T));
   T.err = err;
+  T.wait_ns = o->wait_limit_us > 0 ? 1000ull * (unsigned long long)o->wait_limit_us : kWaitLimitNs;
+  T.withhold = o->test_withhold > 0 ? o->test_withhold - 1 : -1;
   const int hw = WRI_TX + 4, hh = P.by + 2, pr = promo;
   for (int gi = 0; gi < b.ngroups; ++gi) {
     const GroupDev& G = b.g[gi];
@@ -461,64 +512,126 @@ bool build_tma(const Batch& b, const Plan& P, int* err, int promo, TmaSet& T) {
   return true;
 }
 
-// Runs CG iterations (phase 1 + phase 2) in CUDA-graph batches of K until no system remains.
+// Conditional graph nodes (a WHILE node whose condition a device kernel sets) available?
+bool device_loop_supported() {
+  static int ok = -1;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    ok = (cudaGraphCreate(&g, 0) == cudaSuccess &&
+          cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess)
+             ? 1
+             : 0;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+  });
+  return ok == 1;
+}
+
+// Captures K CG iterations (phase 1 + phase 2 launches) on c->cap into whatever capture is open.
+cudaError_t capture_iterations(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, int rb,
+                               bool use_tma, const TmaSet* tma, cudaStream_t cap) {
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < K && err == cudaSuccess; ++k) {
+    if (use_tma) {
+      err = launch_phase_tma(M_P1, P.tma_cfg, b1, *tma, 0, cap);
+      if (err == cudaSuccess) err = launch_phase_tma(M_P2, P.tma_cfg, b2, *tma, 0, cap);
+    } else {
+      err = march(rb, rb, M_P1, false, P.by, b1, cap);
+      if (err == cudaSuccess) err = march(rb, rb, mode2, true, P.by, b2, cap);
+    }
+  }
+  return err;
+}
+
+// Runs CG iterations (phase 1 + phase 2) until no system remains.  The iterations are captured
+// once per batch shape in a CUDA graph whose WHILE node repeats a body of K iterations and a tiny
+// control kernel on the device, with no host round trip; the host reads the counters once at the
+// end.  (Without conditional nodes the graph holds K iterations and the host replays it, reading
+// the counters after every replay.)  The workspace counters are: [0] systems not yet done, [1] the
+// copy-wait error flag, [2] loop bodies run.
 int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, int max_iter, cudaStream_t st,
              const TmaSet* tma = nullptr) {
   DevCtx* c = ctx();
-  if (!c) return WRI_ECUDA;
+  int* slot = poll_slot();
+  if (!c || !slot) return WRI_ECUDA;
   const int rb = P.ir ? 4 : P.vbytes / 2;
   const bool use_tma = tma && P.tma_cfg >= 0 && mode2 == M_P2;
+  const bool dev_loop = device_loop_supported();
+  // loop bodies after which the device loop gives up: every system stops by max_iter + 1 iterations
+  const int cap_bodies = (max_iter + 2 + K - 1) / K + 2;
   // graph lookup / capture
-  std::vector<unsigned char> key(sizeof(Batch) * 2 + 5 * sizeof(int) + (use_tma ? sizeof(TmaSet) : 0));
+  std::vector<unsigned char> key(sizeof(Batch) * 2 + 7 * sizeof(int) + (use_tma ? sizeof(TmaSet) : 0));
   std::memcpy(key.data(), &b1, sizeof(Batch));
   std::memcpy(key.data() + sizeof(Batch), &b2, sizeof(Batch));
-  const int extra[5] = {mode2, K, P.by, rb, use_tma ? P.tma_cfg : -1};
+  const int extra[7] = {mode2, K, P.by, rb, use_tma ? P.tma_cfg : -1, dev_loop ? 1 : 0, cap_bodies};
   std::memcpy(key.data() + 2 * sizeof(Batch), extra, sizeof(extra));
   if (use_tma) std::memcpy(key.data() + 2 * sizeof(Batch) + sizeof(extra), tma, sizeof(TmaSet));
-  cudaGraphExec_t exec = nullptr;
+  std::shared_ptr<CUgraphExec_st> exec;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto& e : c->graphs)
       if (e.key == key) exec = e.exec;
     if (!exec) {
       cudaGraph_t graph = nullptr;
-      WRI_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+      cudaGraphExec_t raw = nullptr;
       cudaError_t err = cudaSuccess;
-      for (int k = 0; k < K && err == cudaSuccess; ++k) {
-        if (use_tma) {
-          err = launch_phase_tma(M_P1, P.tma_cfg, b1, *tma, 0, c->cap);
-          if (err == cudaSuccess) err = launch_phase_tma(M_P2, P.tma_cfg, b2, *tma, 0, c->cap);
-        } else {
-          err = march(rb, rb, M_P1, false, P.by, b1, c->cap);
-          if (err == cudaSuccess) err = march(rb, rb, mode2, true, P.by, b2, c->cap);
+      if (dev_loop) {
+        WRI_CK(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle h;
+        err = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (err == cudaSuccess) err = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        if (err == cudaSuccess) {
+          cudaGraph_t body = np.conditional.phGraph_out[0];
+          err = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+          if (err == cudaSuccess) {
+            err = capture_iterations(P, b1, b2, mode2, K, rb, use_tma, tma, c->cap);
+            if (err == cudaSuccess) err = launch_loop_ctl(h, b1.remaining, cap_bodies, c->cap);
+            const cudaError_t e2 = cudaStreamEndCapture(c->cap, &body);
+            if (err == cudaSuccess) err = e2;
+          }
         }
+      } else {
+        WRI_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+        err = capture_iterations(P, b1, b2, mode2, K, rb, use_tma, tma, c->cap);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+        if (err == cudaSuccess) err = e2;
       }
-      cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
-      if (err != cudaSuccess || e2 != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return WRI_ECUDA;
-      }
-      e2 = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e2 != cudaSuccess) return WRI_ECUDA;
-      if (c->graphs.size() >= 8) {
-        cudaGraphExecDestroy(c->graphs.front().exec);
-        c->graphs.erase(c->graphs.begin());
-      }
+      if (err == cudaSuccess) err = cudaGraphInstantiate(&raw, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (err != cudaSuccess) return WRI_ECUDA;
+      exec = std::shared_ptr<CUgraphExec_st>(raw, [](cudaGraphExec_t x) { cudaGraphExecDestroy(x); });
+      if (c->graphs.size() >= 8) c->graphs.erase(c->graphs.begin());  // freed once no launch holds it
       DevCtx::Entry e;
       e.key = key;
       e.exec = exec;
+      e.device_loop = dev_loop;
       c->graphs.push_back(e);
     }
   }
+  if (dev_loop) {
+    WRI_CK(cudaMemsetAsync(b1.remaining + 2, 0, sizeof(int), st));
+    WRI_CK(cudaGraphLaunch(exec.get(), st));
+    WRI_CK(cudaMemcpyAsync(slot, b1.remaining, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    WRI_CK(cudaStreamSynchronize(st));
+    if (slot[1] != 0) return WRI_ECUDA;  // a bounded copy wait timed out
+    if (slot[0] > 0) return WRI_ECUDA;   // a system failed to stop by max_iter (cannot happen)
+    return WRI_OK;
+  }
   long long launched = 0;
   for (;;) {
-    WRI_CK(cudaGraphLaunch(exec, st));
+    WRI_CK(cudaGraphLaunch(exec.get(), st));
     launched += K;
-    WRI_CK(cudaMemcpyAsync(c->pinned, b1.remaining, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    WRI_CK(cudaMemcpyAsync(slot, b1.remaining, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     WRI_CK(cudaStreamSynchronize(st));
-    if (c->pinned[1] != 0) return WRI_ECUDA;  // a bounded copy wait timed out
-    if (*c->pinned <= 0) break;
+    if (slot[1] != 0) return WRI_ECUDA;  // a bounded copy wait timed out
+    if (slot[0] <= 0) break;
     if (launched > (long long)max_iter + 2 * K + 2) return WRI_ECUDA;  // a system failed to stop
   }
   return WRI_OK;
@@ -545,8 +658,9 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   b.max_iter = o->max_iter;
   b.tol = o->tol;
   const int vb = P.vbytes / 2;
+  if (setup_rmask(P, b, ws, st) != WRI_OK) return WRI_ECUDA;
   WRI_CK(launch_setup_rhs(o->dtype == WRI_C128 ? 8 : 4, vb, b, P.nsys_total, st));
-  WRI_CK(cudaMemsetAsync(b.remaining, 0, 2 * sizeof(int), st));
+  WRI_CK(cudaMemsetAsync(b.remaining, 0, 3 * sizeof(int), st));
   if (o->warm_start) {
     Batch r = b;
     r.flavor = SH_REF;
@@ -569,7 +683,7 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   if (P.tma_cfg >= 0) {
     WRI_CK(launch_ztable(b, st));
     static thread_local TmaSet T;  // ~8 KB: kept off the stack
-    if (build_tma(b, P, b.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, T))
+    if (build_tma(b, P, b.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, o, T))
       return run_loop(P, b1, b2, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, &T);
     // descriptors rejected (e.g. an unaligned model array): same decomposition, z-march kernels
   }
@@ -585,8 +699,8 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
 // scales with u32 kappa(S), not with u32 kappa(S)^2 as for refinement on the normal equations.
 int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o, const Plan& P, char* ws,
                   cudaStream_t st) {
-  DevCtx* c = ctx();
-  if (!c) return WRI_ECUDA;
+  int* slot = poll_slot();
+  if (!slot) return WRI_ECUDA;
   // FP64 views: the residual kernel reads x64 and writes q64 (nodes) and b.r2 = q2 (receivers)
   Batch outer = solver_batch(groups, P, ws, false);
   for (int gi = 0; gi < P.ngroups; ++gi) {
@@ -605,6 +719,7 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
   // complex64 views: x = dx, r2 = r2_in, gvec = g'
   Batch inner = solver_batch(groups, P, ws, true);
   inner.max_iter = o->max_iter;
+  if (setup_rmask(P, inner, ws, st) != WRI_OK) return WRI_ECUDA;
   void* u[WRI_MAXG] = {};
   for (int gi = 0; gi < P.ngroups; ++gi) u[gi] = groups[gi].u;
   // lambda d in FP64 (lamd and q2), x64 = warm ? u : 0, r64 = 0, dx = 0
@@ -632,22 +747,29 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
     inner.order = (ord == 1) ? 1 : (ord == 3) ? 2 : (ord >= 4) ? 3 : 0;
     inner.sblock = (ord >= 4) ? (1 << (ord - 2)) : 1;
     WRI_CK(launch_ztable(inner, st));
-    if (build_tma(inner, P, inner.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, T))
+    if (build_tma(inner, P, inner.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, o, T))
       tma = &T;
   }
   for (int outer_k = 0;; ++outer_k) {
-    WRI_CK(cudaMemsetAsync(outer.remaining, 0, 2 * sizeof(int), st));
+    WRI_CK(cudaMemsetAsync(outer.remaining, 0, 3 * sizeof(int), st));
     Batch r = outer;
     r.outer = outer_k;
     r.flavor = SH_REFINE;
     WRI_CK(march(8, 8, M_RES, false, P.by, r, st));                // q = b - S x64
     WRI_CK(launch_ir_forcing(inner, outer.r2, st));                // f = q - r64 (complex64)
     WRI_CK(launch_march_f64_to_f32(M_SH, P.by, r, 0, st));         // c = S^H q, outer test
-    WRI_CK(cudaMemcpyAsync(c->pinned, outer.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WRI_CK(cudaMemcpyAsync(slot, outer.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
     WRI_CK(cudaStreamSynchronize(st));
-    if (*c->pinned <= 0) break;
-    WRI_CK(launch_march_f64_to_f32(M_SH, P.by, gb, 0, st));        // g' = S^H r64
-    const int rc = run_loop(P, inner, inner, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, tma);
+    if (*slot <= 0) break;
+    Batch in = inner;
+    if (outer_k == 0) {
+      // r64 = 0 (k_ir_init), so g' = S^H r64 = 0: the first inner solve is plain CGLS, and its
+      // phase 2 reads no g'
+      for (int gi = 0; gi < P.ngroups; ++gi) in.g[gi].gvec = nullptr;
+    } else {
+      WRI_CK(launch_march_f64_to_f32(M_SH, P.by, gb, 0, st));      // g' = S^H r64
+    }
+    const int rc = run_loop(P, in, in, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, tma);
     if (rc != WRI_OK) return rc;
     WRI_CK(launch_ir_update(inner, st));                           // x64 += dx, r64 += dr
     if (outer_k > o->max_refine + 1) return WRI_ECUDA;
@@ -661,8 +783,9 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
 // back by the host.  Iterates and stopping rule are those of the fused path.
 int solve_plain(const wri_group* groups, int ngroups, const wri_solve_opts* o, const Plan& P, char* ws,
                 int32_t* iters, double* relres, int32_t* status, cudaStream_t st) {
-  DevCtx* c = ctx();
-  if (!c) return WRI_ECUDA;
+  int* slot = poll_slot();
+  if (!slot) return WRI_ECUDA;
+  double* pinned_d = (double*)(slot + 4);
   const int rb = P.vbytes / 2;
   const size_t cb = P.vbytes;
   double* part = (double*)(ws + P.off_part);
@@ -713,19 +836,19 @@ int solve_plain(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
       auto dot2 = [&](const void* v1, long long n1, const void* v2, long long n2, double& out) -> int {
         WRI_CK(plain_dot(rb, v1, n1, part, dres, st));
         if (v2 && n2 > 0) WRI_CK(plain_dot(rb, v2, n2, part, dres + 1, st));
-        WRI_CK(cudaMemcpyAsync(c->pinned_d, dres, sizeof(double) * ((v2 && n2 > 0) ? 2 : 1),
+        WRI_CK(cudaMemcpyAsync(pinned_d, dres, sizeof(double) * ((v2 && n2 > 0) ? 2 : 1),
                                cudaMemcpyDeviceToHost, st));
         WRI_CK(cudaStreamSynchronize(st));
-        out = c->pinned_d[0] + ((v2 && n2 > 0) ? c->pinned_d[1] : 0.0);
+        out = pinned_d[0] + ((v2 && n2 > 0) ? pinned_d[1] : 0.0);
         return WRI_OK;
       };
       // b1 = alpha e (known weight) or 0; the weight lives on the device
       double ar = 0.0, ai = 0.0;
       if (U.alpha) {
-        WRI_CK(cudaMemcpyAsync(c->pinned_d, U.alpha + 2 * l, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        WRI_CK(cudaMemcpyAsync(pinned_d, U.alpha + 2 * l, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         WRI_CK(cudaStreamSynchronize(st));
-        ar = c->pinned_d[0];
-        ai = c->pinned_d[1];
+        ar = pinned_d[0];
+        ai = pinned_d[1];
       }
       WRI_CK(plain_fill(rb, r1, x, n, U.alpha ? sd.src : -1, ar, ai, st));
       WRI_CK(plain_setr2(rb, r2, dd, nr, U.lambda, st));
@@ -1047,12 +1170,15 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
   rc = validate_groups(groups, ngroups, true);
   if (rc != WRI_OK) return rc;
   if (trial_iters < 2) return WRI_EINVAL;
-  if (opts->dtype != WRI_C64 || opts->max_refine > 0 || opts->plain || opts->kernel == 1) return WRI_OK;
+  if (opts->dtype != WRI_C64 || opts->plain || opts->kernel == 1) return WRI_OK;
   for (int gi = 0; gi < ngroups; ++gi)
     if (groups[gi].grid.nx % 4 != 0 || (uintptr_t)groups[gi].u % 16 != 0) return WRI_OK;
+  // with refinement the inner solves run on the warp-specialised kernels only (their phase 2 adds
+  // S^H r64); the trials are plain CGLS solves on those kernels
+  const bool refine = opts->max_refine > 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return WRI_ECUDA;
-  std::vector<long long> key = {dev, ngroups};
+  std::vector<long long> key = {dev, ngroups, refine ? 1 : 0};
   for (int gi = 0; gi < ngroups; ++gi) {
     const wri_group& G = groups[gi];
     key.insert(key.end(), {G.grid.nx, G.grid.ny, G.grid.nz, G.nsys, G.rec_off[G.nsys]});
@@ -1079,6 +1205,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
   int best_kernel = 0, best_order = 0;
   rc = WRI_OK;
   for (int cfg : kCfgs) {
+    if (refine && cfg < kFirstWsCfg) continue;
     for (int ord : kOrders) {
       wri_solve_opts o = *opts;
       o.kernel = 2 + cfg;
@@ -1086,6 +1213,8 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
       o.tol = 0.0;
       o.warm_start = 0;
       o.max_iter = trial_iters;
+      o.max_refine = 0;
+      o.test_withhold = 0;
       Plan P;
       plan_solve(groups, ngroups, &o, P);
       if (P.tma_cfg != cfg || check_ws(P, workspace, ws_bytes) != WRI_OK) continue;

@@ -151,6 +151,9 @@ struct GroupDev {
   const void* gvec;         // [nsys][n] complex64 S^H r64, added to s in phase 2 (or null)
   const int* rmap;          // [nsys][n] receiver entry of a node (-1: none): the FP64 S^H kernels of
                             // the refinement add lambda P^T r2 in the stencil pass (or null)
+  const uint32_t* rmask;    // [nsys][nz][ny][tiles_x] receiver bits of the normal-residual norms
+                            // (bit b of word (k, j, t): node (32 t + b, j, k) is a receiver), or null
+  const uint32_t* rcol;     // [nsys][ny][tiles_x] OR of rmask over k (columns holding a receiver)
   double* grad;             // [n] gradient accumulator (gradient kernel only)
   const float2* ztab;       // [2][nz][3] z-axis coefficients (s_z, 1/(s_z(k-1/2) h^2), 1/(s_z(k+1/2) h^2)),
                             // [0] for A, [1] conjugated for A^H; FP32, built once per solve

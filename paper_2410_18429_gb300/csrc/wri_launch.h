@@ -17,6 +17,10 @@ cudaError_t launch_march_f64_to_f32(int mode, int by, const Batch& b, int grid, 
 // small kernels (wri_small.cu)
 cudaError_t launch_setup_rhs(int dtype_bytes, int rl_bytes, const Batch& b, int nsys_total, cudaStream_t st);
 cudaError_t launch_ztable(const Batch& b, cudaStream_t st);
+// receiver bitmaps of every group (b: solver view with rmask / rcol set and zeroed)
+cudaError_t launch_rmask(const Batch& b, int nsys_total, cudaStream_t st);
+// control kernel of the device-side CG loop (one thread; sets the WHILE node's condition)
+cudaError_t launch_loop_ctl(cudaGraphConditionalHandle h, int* counters, int cap, cudaStream_t st);
 cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* relres, int32_t* status,
                           cudaStream_t st);
 // FP64 refinement (b: inner complex64 view; u: the caller's wavefields, one per group)

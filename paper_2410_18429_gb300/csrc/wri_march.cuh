@@ -102,6 +102,22 @@ __device__ __forceinline__ ZCoef<R> z_coef(const GroupDev& G, int k) {
   return c;
 }
 
+// Receiver nodes in the normal-residual norms ||S^H r||^2.  At a receiver node of system sl the
+// finalizer adds lambda P^T r2 to the stencil value A^H r1 and accounts |s|^2 of the sum itself,
+// so the stencil passes leave those nodes out of their partial sums.  (Summing |A^H r1|^2 over
+// every node and correcting by |s|^2 - |A^H r1|^2 afterwards cancels catastrophically near
+// convergence, where A^H r1 and -lambda P^T r2 are large and nearly equal at the receivers: the
+// norm of a converged complex128 solve came out as exactly 0.)
+// Bits of the thread's 32-node row segment (x0 .. x0+31, row j) that hold a receiver at any z ...
+__device__ __forceinline__ uint32_t rec_col_bits(const GroupDev& G, int sl, int j, int x0) {
+  if (!G.rmask) return 0u;
+  return __ldg(G.rcol + ((long long)sl * G.ny + j) * G.tiles_x + (x0 >> 5));
+}
+// ... and at plane k
+__device__ __forceinline__ uint32_t rec_plane_bits(const GroupDev& G, int sl, int k, int j, int x0) {
+  return __ldg(G.rmask + (((long long)sl * G.nz + k) * G.ny + j) * G.tiles_x + (x0 >> 5));
+}
+
 // First/last node index of an axis whose own stretch and both half-point stretches are 1.
 __device__ __forceinline__ void interior_range(const AxisPml& a, int& lo, int& hi) {
   if (a.npml > 0) {

@@ -63,7 +63,8 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
       const C add = lam * r2[k];
       const OC sn = to_c(to_c(sv, R(0)) + add, OR(0));
       S[node] = sn;
-      rec += (double)abs2(sn) - (double)abs2(sv);
+      // the stencil pass left receiver nodes out of its partial sums (rec_col_bits)
+      rec += (double)abs2(sn);
     } else if (MODE == M_RES) {
       const C xv = ldcg_c((const C*)G.x + node);
       r2[k] = ((const C*)b.lamd)[k] - lam * xv;
@@ -272,6 +273,9 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
         SysDev* sdl = (MODE == M_APPLY) ? nullptr : b.sys + (G.sys0 + sl);
         const long long src = (MODE == M_APPLY) ? -1 : sdl->src;
         const int cur = (MODE == M_P1 || MODE == M_P2) ? (sd->iter & 1) : 0;
+        // receivers of this system in this thread's column (left out of the norm, rec_col_bits)
+        const uint32_t rcb = ((MODE == M_P2 || (MODE == M_SH && !G.rmap)) && own)
+                                 ? (rec_col_bits(G, sl, j, x0) >> tx) & 1u : 0u;
 
         // field F = Fa + coef * Fb, or the point field b1 = alpha e (cold start)
         const bool point = (MODE == M_SH) && (b.flavor == SH_INIT || b.flavor == SH_REF);
@@ -395,8 +399,10 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
                 if (rk >= 0) AF = AF + R(G.lambda) * ((const C*)b.r2)[rk];
               }
               ((OC*)G.s)[gnode] = to_c(AF, OR(0));
-              if (sizeof(R) == 4) accf += (float)abs2(AF);
-              else accd += (double)abs2(AF);
+              if (!(rcb && ((rec_plane_bits(G, sl, k, j, x0) >> tx) & 1u))) {
+                if (sizeof(R) == 4) accf += (float)abs2(AF);
+                else accd += (double)abs2(AF);
+              }
             } else if (MODE == M_RES) {
               C r = czero<R>() - AF;
               if (node == src) r = G.masked ? czero<R>() : a_src - AF;
@@ -411,8 +417,10 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
               // system S^H S dx = S^H f - g with g = -S^H r64
               if (G.gvec) AF = AF + to_c(((const float2*)G.gvec)[gnode], R(0));
               ((C*)G.s)[gnode] = AF;
-              if (sizeof(R) == 4) accf += (float)abs2(AF);
-              else accd += (double)abs2(AF);
+              if (!(rcb && ((rec_plane_bits(G, sl, k, j, x0) >> tx) & 1u))) {
+                if (sizeof(R) == 4) accf += (float)abs2(AF);
+                else accd += (double)abs2(AF);
+              }
             } else if (MODE == M_GRAD) {
               C r = AF;
               if (node == src) r = r - a_src;

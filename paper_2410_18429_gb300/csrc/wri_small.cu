@@ -21,6 +21,17 @@ cudaError_t launch_setup_rhs(int dtype_bytes, int rl_bytes, const Batch& b, int 
   return cudaGetLastError();
 }
 
+cudaError_t launch_rmask(const Batch& b, int nsys_total, cudaStream_t st) {
+  if (nsys_total <= 0) return cudaSuccess;
+  k_rmask<<<nsys_total, 128, 0, st>>>(b, nsys_total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_ctl(cudaGraphConditionalHandle h, int* counters, int cap, cudaStream_t st) {
+  k_loop_ctl<<<1, 1, 0, st>>>(h, counters, cap);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ztable(const Batch& b, cudaStream_t st) {
   k_ztable<<<dim3(4, b.ngroups), 128, 0, st>>>(b);
   return cudaGetLastError();

@@ -27,6 +27,38 @@ __global__ void k_setup_rhs(const __grid_constant__ Batch b, int nsys_total) {
   }
 }
 
+// Receiver bitmaps of the normal-residual norms (rec_col_bits): one block per system; the
+// caller zeroed both maps.  Receivers are distinct within a system, so every bit is set once.
+__global__ void k_rmask(const __grid_constant__ Batch b, int nsys_total) {
+  const int s = blockIdx.x;
+  if (s >= nsys_total) return;
+  const SysDev& sd = b.sys[s];
+  const GroupDev& G = b.g[sd.group];
+  if (!G.rmask) return;
+  uint32_t* mask = const_cast<uint32_t*>(G.rmask);
+  uint32_t* col = const_cast<uint32_t*>(G.rcol);
+  const long long plane = (long long)G.nx * G.ny;
+  for (int k = sd.rec_begin + threadIdx.x; k < sd.rec_end; k += blockDim.x) {
+    const long long node = b.rec_idx[k];
+    const int z = (int)(node / plane);
+    const long long rem = node - (long long)z * plane;
+    const int y = (int)(rem / G.nx);
+    const int x = (int)(rem - (long long)y * G.nx);
+    const uint32_t bit = 1u << (x & 31);
+    atomicOr(mask + (((long long)sd.local * G.nz + z) * G.ny + y) * G.tiles_x + (x >> 5), bit);
+    atomicOr(col + ((long long)sd.local * G.ny + y) * G.tiles_x + (x >> 5), bit);
+  }
+}
+
+// Control kernel of the device-side CG loop (the WHILE node of the iteration graph): the body runs
+// again while systems remain, no copy wait has timed out and fewer than `cap` bodies have run.
+// counters: [0] systems not done, [1] copy-wait error flag, [2] bodies run (zeroed per solve).
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, int* counters, int cap) {
+  const int body = ++counters[2];
+  const bool go = counters[0] > 0 && counters[1] == 0 && body < cap;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // z-axis coefficient tables of every group (FP32): one thread per (group, plane).
 __global__ void k_ztable(const __grid_constant__ Batch b) {
   const int g = blockIdx.y;

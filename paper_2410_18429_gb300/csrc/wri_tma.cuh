@@ -26,7 +26,11 @@ enum TmaMap : int { TM_S = 0, TM_P0, TM_P1, TM_X, TM_T1, TM_R0, TM_R1, TM_M, TM_
 
 struct TmaSet {
   CUtensorMap map[WRI_MAXG][TM_COUNT];
-  int* err;  // set to 1 by a CTA whose copy wait timed out
+  int* err;                // set to 1 by a CTA whose copy wait timed out
+  unsigned long long wait_ns;  // time limit of every copy-pipeline wait (global timer, ns)
+  int withhold;            // test hook, -1 = off: the copy warp of CTA 0 never issues its fill of this
+                           // index, so the consumers' wait for it runs out (the bounded-wait path)
+  int pad_;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -56,16 +60,17 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Time limit of every wait of the copy pipelines: only a copy that never completes (a broken
-// descriptor or protocol) can reach it.
+// Default time limit of every wait of the copy pipelines (TmaSet::wait_ns): only a copy that
+// never completes (a broken descriptor or protocol, or the withheld fill of the test hook) can
+// reach it.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
-// bounded wait: false after 2 s of polling (or 2^26 polls, whichever comes first)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait: false after `limit` ns of polling (or 2^26 polls, whichever comes first)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit) {
   const uint64_t t0 = global_ns();
   for (int i = 0; i < (1 << 26); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) return false;
+    if ((i & 255) == 255 && global_ns() - t0 > limit) return false;
   }
   return false;
 }
@@ -229,6 +234,8 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
         src_col = sd->src - (long long)src_k * plane;
       }
       const bool own_src_col = (src_col == col);
+      // receivers of this system in the thread's column: left out of the phase-2 norm
+      const uint32_t rcb = (MODE == M_P2 && own) ? (rec_col_bits(G, sl, j, x0) >> tx) & 1u : 0u;
       const int count = z1 - z0 + 2;  // planes z0-1 .. z1
 
       auto issue = [&](int q) {
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
         const uint32_t par = ((uses + q) / S) & 1u;
         // every thread waits for the stage itself; a time-out is made uniform at the
         // plane barrier below (the F values of a failed plane are never used)
-        if (!mbar_wait(&bar[st], par)) s_abort = 1;
+        if (!mbar_wait(&bar[st], par, T.wait_ns)) s_abort = 1;
         const unsigned char* base = smem + (size_t)st * L::STAGE;
         const C* A = reinterpret_cast<const C*>(base);
         const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
             C o = AF;
             if (MODE == M_P1 && own_src_col && kp == src_k) o = czero<float>();
             pO[po - plane] = o;
-            acc.add(abs2(o));
+            if (!(rcb && ((rec_plane_bits(G, sl, kp, j, x0) >> tx) & 1u))) acc.add(abs2(o));
           }
         }
         m_prev = m_new;
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(WRI_TX* BY, MINB) k_phase_tma(const __grid_con
         // a copy never completed: record it, drain the copies this CTA issued (bounded), stop
         if (tid == 0) {
           atomicExch(T.err, 1);
-          for (int qq = q_fail; qq < issued; ++qq) mbar_wait(&bar[(uses + qq) % S], ((uses + qq) / S) & 1u);
+          for (int qq = q_fail; qq < issued; ++qq) mbar_wait(&bar[(uses + qq) % S], ((uses + qq) / S) & 1u, T.wait_ns);
         }
         __syncthreads();
         return;
@@ -494,6 +501,8 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
         src_col = sd->src - (long long)src_k * plane;
       }
       const int src_lane = (src_col == col) ? 0 : (src_col == col + 1) ? 1 : -1;
+      // receivers of this system in the thread's two columns: left out of the phase-2 norm
+      const uint32_t rcb = (MODE == M_P2 && own) ? (rec_col_bits(G, sl, j, x0) >> (2 * tx)) & 3u : 0u;
       const int count = z1 - z0 + 2;
 
       auto issue = [&](int q) {
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
       for (int q = 0; q < count; ++q, po += plane) {
         const int st = (int)((uses + q) % S);
         const uint32_t par = ((uses + q) / S) & 1u;
-        if (!mbar_wait(&bar[st], par)) s_abort = 1;
+        if (!mbar_wait(&bar[st], par, T.wait_ns)) s_abort = 1;
         const unsigned char* base = smem + (size_t)st * L::STAGE;
         const C* A = reinterpret_cast<const C*>(base);
         const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
@@ -655,8 +664,14 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
               if (src_lane == 1) a1 = czero<float>();
             }
             st4(pO + po - plane, a0, a1);
-            acc.add(abs2(a0));
-            acc.add(abs2(a1));
+            float e0 = abs2(a0), e1 = abs2(a1);
+            if (rcb) {
+              const uint32_t w = rec_plane_bits(G, sl, kp, j, x0) >> (2 * tx);
+              if (w & 1u) e0 = 0.f;
+              if (w & 2u) e1 = 0.f;
+            }
+            acc.add(e0);
+            acc.add(e1);
           }
         }
         m_prev = m_new;
@@ -664,7 +679,7 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
       if (q_fail >= 0) {
         if (tid == 0) {
           atomicExch(T.err, 1);
-          for (int qq = q_fail; qq < issued; ++qq) mbar_wait(&bar[(uses + qq) % S], ((uses + qq) / S) & 1u);
+          for (int qq = q_fail; qq < issued; ++qq) mbar_wait(&bar[(uses + qq) % S], ((uses + qq) / S) & 1u, T.wait_ns);
         }
         __syncthreads();
         return;
@@ -721,11 +736,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // bounded wait that also gives up as soon as another role raised the abort flag
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort_flag,
+                                                   uint64_t limit) {
   const uint64_t t0 = global_ns();
   for (int i = 0; i < (1 << 26); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 63 && (*abort_flag || global_ns() - t0 > kWaitLimitNs)) return false;
+    if ((i & 63) == 63 && (*abort_flag || global_ns() - t0 > limit)) return false;
   }
   return false;
 }
@@ -791,9 +807,12 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCW);
     }
-    s_abort = 0;
+    // a copy wait of an earlier launch of this solve timed out: the solve is being stopped, and
+    // this launch does nothing (read once here so that the whole CTA takes the same decision)
+    s_abort = (*(volatile const int*)T.err != 0) ? 1 : 0;
   }
   __syncthreads();  // the only CTA-wide barrier: the copy warp leaves the consumers' barriers after it
+  if (s_abort) return;
 
   // ================================================================ copy warp
   if (PW && tid >= NC) {
@@ -825,7 +844,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
       const int count = z1 - z0 + 2;
       for (int q = 0; q < count; ++q, ++fills) {
         const int st = (int)(fills % S);
-        if (fills >= (unsigned)S && !mbar_wait_or_abort(&empty[st], ((fills / S) - 1) & 1u, &s_abort)) {
+        if (fills >= (unsigned)S && !mbar_wait_or_abort(&empty[st], ((fills / S) - 1) & 1u, &s_abort, T.wait_ns)) {
           s_abort = 1;
           atomicExch(T.err, 1);
           stop = true;
@@ -835,6 +854,9 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
           stop = true;
           break;
         }
+        // test hook (off unless the caller asks): this fill is never issued, so its "full" barrier
+        // never completes and the consumers' bounded wait for it runs out
+        if (blockIdx.x == 0 && (int)fills == T.withhold) continue;
         unsigned char* base = smem + (size_t)st * L::STAGE;
         const int kq = z0 - 1 + q;
         mbar_expect_tx(&full[st], tx_bytes);
@@ -847,7 +869,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
     if (stop) {
       // wait (bounded) until every copy issued into the ring has landed
       const unsigned first = fills > (unsigned)S ? fills - S : 0u;
-      for (unsigned u = first; u < fills; ++u) mbar_wait(&full[u % S], (u / S) & 1u);
+      for (unsigned u = first; u < fills; ++u) mbar_wait(&full[u % S], (u / S) & 1u, T.wait_ns);
     }
     return;
   }
@@ -912,12 +934,14 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         src_col = sd->src - (long long)src_k * plane;
       }
       const int src_lane = (src_col == col) ? 0 : (src_col == col + 1) ? 1 : -1;
+      // receivers of this system in the thread's two columns: left out of the phase-2 norm
+      const uint32_t rcb = (MODE == M_P2 && own) ? (rec_col_bits(G, sl, j, x0) >> (2 * tx)) & 3u : 0u;
       const int count = z1 - z0 + 2;
       // PW = false: thread 0 issues fill q of this item (plane z0 - 1 + q) into stage (fills + q) % S
       auto fill = [&](int q) {
         const unsigned u = fills + (unsigned)q;
         const int st = (int)(u % S);
-        if (u >= (unsigned)S && !mbar_wait_or_abort(&empty[st], ((u / S) - 1) & 1u, &s_abort)) {
+        if (u >= (unsigned)S && !mbar_wait_or_abort(&empty[st], ((u / S) - 1) & 1u, &s_abort, T.wait_ns)) {
           s_abort = 1;
           atomicExch(T.err, 1);
           return;
@@ -977,7 +1001,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
           const int st = (int)(u % S);
           bool ok = true;
           if (!s_abort) {
-            ok = mbar_wait_or_abort(&full[st], (u / S) & 1u, &s_abort);
+            ok = mbar_wait_or_abort(&full[st], (u / S) & 1u, &s_abort, T.wait_ns);
             if (!ok) {
               s_abort = 1;
               atomicExch(T.err, 1);
@@ -1019,7 +1043,13 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
                 a1 = a1 + hi2(gv);
               }
               st4(pO + po - plane, a0, a1);
-              accf += abs2(a0) + abs2(a1);
+              float e0 = abs2(a0), e1 = abs2(a1);
+              if (rcb) {
+                const uint32_t w = rec_plane_bits(G, sl, kq - 1, j, x0) >> (2 * tx);
+                if (w & 1u) e0 = 0.f;
+                if (w & 2u) e1 = 0.f;
+              }
+              accf += e0 + e1;
             }
             if (q >= 1 && q <= count - 2) {
               // plane kq: every stencil term but the z+1 one, from this stage and registers
@@ -1109,7 +1139,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         const int st = (int)(u % S);
         bool ok = true;
         if (!s_abort) {
-          ok = mbar_wait_or_abort(&full[st], (u / S) & 1u, &s_abort);
+          ok = mbar_wait_or_abort(&full[st], (u / S) & 1u, &s_abort, T.wait_ns);
           if (!ok) {
             s_abort = 1;
             atomicExch(T.err, 1);
@@ -1214,7 +1244,13 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
                 a1 = a1 + hi2(gv);
               }
               st4(pO + po - plane, a0, a1);
-              accf += abs2(a0) + abs2(a1);
+              float e0 = abs2(a0), e1 = abs2(a1);
+              if (rcb) {
+                const uint32_t w = rec_plane_bits(G, sl, kp, j, x0) >> (2 * tx);
+                if (w & 1u) e0 = 0.f;
+                if (w & 2u) e1 = 0.f;
+              }
+              accf += e0 + e1;
             }
           }
         }
@@ -1258,7 +1294,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
   if (!PW && tid == 0 && s_abort) {
     // stopped early: wait (bounded) until every copy thread 0 issued has landed
     const unsigned first = issued > (unsigned)S ? issued - S : 0u;
-    for (unsigned u = first; u < issued; ++u) mbar_wait(&full[u % S], (u / S) & 1u);
+    for (unsigned u = first; u < issued; ++u) mbar_wait(&full[u % S], (u / S) & 1u, T.wait_ns);
   }
 }
 

@@ -115,14 +115,19 @@ def test_apply_rejects_overlap_and_bad_grid(W):
 
 def test_autotune_validates_and_skips_unsupported_batches(W):
     """Argument errors come back before any device work; batches the TMA phases cannot take
-    (complex128, refinement, the baseline path) return unchanged without touching the device."""
+    (complex128, the baseline path, the z-march kernels) return unchanged without touching the
+    device.  (Refined batches are tuned: their inner solves run on the TMA phases.)"""
     m = W._Marshal([_spec(W)])
     o = W.make_opts()
     assert W.lib.wri_autotune(m.arr, m.n, C.byref(o), 1, 0x1000, 1 << 30, None) == W.EINVAL
     assert W.lib.wri_autotune(m.arr, m.n, None, 8, 0x1000, 1 << 30, None) == W.EINVAL
     bad = W._Marshal([_spec(W, nx=2)])
     assert W.lib.wri_autotune(bad.arr, bad.n, C.byref(o), 8, 0x1000, 1 << 30, None) == W.EINVAL
-    for kw in (dict(dtype=W.C128), dict(max_refine=2), dict(plain=True), dict(kernel=W.KERNEL_MARCH)):
+    for kw in (dict(wait_limit_us=-1), dict(test_withhold=-2)):
+        assert W.lib.wri_autotune(m.arr, m.n, C.byref(W.make_opts(**kw)), 8, 0x1000, 1 << 30, None) == W.EINVAL
+        assert W.lib.wri_solve_batch(m.arr, m.n, C.byref(W.make_opts(**kw)), 0x100, 0x200, 0x300, 0x1000, 1 << 40,
+                                     None) == W.EINVAL
+    for kw in (dict(dtype=W.C128), dict(plain=True), dict(kernel=W.KERNEL_MARCH)):
         o2 = W.make_opts(**kw)
         before = bytes(o2)
         assert W.lib.wri_autotune(m.arr, m.n, C.byref(o2), 8, 0x1000, 1 << 30, None) == W.OK
