@@ -4,9 +4,18 @@ Configuration 1 (plain SF-AWRI, one solve + gradient): 24^3 physical nodes + 6-c
 h = 10 m, homogeneous 2000 m/s inversion model, 5 Hz, one source at (12, 12, 2), 20 receivers at
 x = y = 18, z = 2..21, lambda = 10, complex128, tolerance 1e-8.  The observed data come from an
 exact forward solve (sparse LU) on the true model, a +10 % Gaussian anomaly of sigma 3 cells, with
-the true weight -10 (the 5 Hz weight of Table SrcCam).  The oracle's exact (LU) evaluation of the
-same problem is the reference: wavefield within 1e-5 and gradient within 1e-4 (relative L2).
+the true weight -10 (the 5 Hz weight of Table SrcCam).
+
+With lambda = 10 this system is stiff: the oracle's own complex128 CGLS stopped at the stated
+1e-8 is still 5e-3 from the exact wavefield and 100 % off in the gradient (tests/golden/
+config1_oracle.json, written by make_config1_oracle.py from oracle/ only).  So the test checks
+two things: at 1e-8 the GPU solve behaves like the oracle's CGLS (iterations within 5 %, the same
+distance to the exact wavefield within 2x), and at 1e-13, where the oracle's CGLS reaches the
+exact evaluation, the GPU wavefield is within 1e-5 and its gradient within 1e-4 of it.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +25,8 @@ from wri_cases import rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config1_oracle.json")
 
 
 @pytest.fixture(scope="module")
@@ -30,24 +41,31 @@ def W():
 
 def test_config1_solve_and_gradient_match_exact(W):
     from paper_2410_18429_gb300.problem import to_device
+    ref = {s["tol"]: s for s in json.load(open(GOLDEN))["solves"]}
     G = synth.workload_c1()
     shp, h, npml = G.spec.shape, G.spec.h, G.spec.npml
     m_true = synth.to_m(synth.workload_c1_true_velocity())
     G.d = O.forward_data(shp, h, G.omega, m_true, npml, G.v_max, G.src, G.rec_off, G.rec_idx, G.alpha)
-    spec = to_device(G, W.C128, "cuda")
-    tol = 1e-8
-    it, rr, st = W.solve([spec], W.make_opts(tol=tol, max_iter=500000, dtype=W.C128))
-    assert st.cpu().tolist() == [W.SYS_OK]
-    assert 0 < float(rr[0]) <= tol
-    a = W.source_estimate([spec], W.C128)
-    g, f = W.gradient([spec], W.C128, a)
     u_ex, a_ex, f_ex, g_ex = O.evaluate(shp, h, G.omega, G.m, npml, G.v_max, G.src, G.rec_off, G.rec_idx,
                                         G.d, G.lam)
+    assert f_ex > 0 and np.linalg.norm(g_ex) > 0   # the homogeneous model is not the true one
+    spec = to_device(G, W.C128, "cuda")
+    # the stated tolerance: the GPU's CGLS follows the oracle's
+    o = ref[1e-8]
+    it, rr, st = W.solve([spec], W.make_opts(tol=1e-8, max_iter=500000, dtype=W.C128))
+    assert st.cpu().tolist() == [W.SYS_OK] and 0 < float(rr[0]) <= 1e-8
+    assert abs(int(it[0]) - o["iterations"]) <= 0.05 * o["iterations"], (int(it[0]), o["iterations"])
+    err_u = rel(spec.u.cpu().numpy(), u_ex)
+    assert 0.5 * o["u_err_vs_exact"] <= err_u <= 2 * o["u_err_vs_exact"], (err_u, o["u_err_vs_exact"])
+    # converged: the wavefield, weight, objective and gradient of the exact evaluation
+    spec.u.zero_()
+    it, rr, st = W.solve([spec], W.make_opts(tol=1e-13, max_iter=1000000, dtype=W.C128))
+    assert st.cpu().tolist() == [W.SYS_OK] and 0 < float(rr[0]) <= 1e-13
+    a = W.source_estimate([spec], W.C128)
+    g, f = W.gradient([spec], W.C128, a)
     err_u = rel(spec.u.cpu().numpy(), u_ex)
     err_g = rel(g[0].cpu().numpy().ravel(), g_ex)
     assert err_u < 1e-5, err_u
     assert rel(a.cpu().numpy(), a_ex) < 1e-5
     assert err_g < 1e-4, err_g
     assert abs(f.item() - f_ex) <= 1e-4 * abs(f_ex)
-    # the homogeneous model is not the true one: the data misfit and the gradient are not zero
-    assert f_ex > 0 and np.linalg.norm(g_ex) > 0
