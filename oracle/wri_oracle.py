@@ -36,7 +36,7 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "stretch", "helmholtz_matrix", "apply_helmholtz", "restriction", "unit_vector",
     "augmented_operator", "rhs", "solve_kkt", "solve_dataspace", "solve_dense", "stretch_weight", "cgls", "source_estimate",
-    "objective", "gradient", "solve_system", "evaluate", "forward_data", "total_variation",
+    "objective", "gradient", "solve_system", "evaluate", "fwi_evaluate", "forward_data", "total_variation",
 ]
 
 
@@ -317,6 +317,40 @@ def evaluate(shape, h, omega, m, npml, v_max, srcs, rec_off, rec_idx, d, lam, al
         P = restriction(n, rec)
         f += objective(A, P, u, srcs[s], ds, lam, a)
         g += gradient(A, u, srcs[s], a, omega, w)
+        us.append(u)
+        als.append(a)
+    return np.array(us), np.array(als), f, g
+
+
+def fwi_evaluate(shape, h, omega, m, npml, v_max, srcs, rec_off, rec_idx, d, alpha=None, R=1e-3):
+    """Reduced FWI, the paper's comparison method (Eqs. PDEsolve and FWI2), by exact LU solves.
+
+    Per system: G = A^{-1} e, the weight a (given, or source-free the minimiser of
+    ||a P G - d||: a = (P G)^H d / ||P G||^2), u = a G (Eq. PDEsolve), the data residual
+    r = P u - d, f = 1/2 sum ||r||^2 (Eq. FWI2), and the adjoint-state gradient
+    g = -omega^2 sum Re(w u conj(v)) with v = A^{-H} P^T r (dA/dm_k = omega^2 w_k e_k e_k^T; the
+    weight's own derivative vanishes at its optimum).  Returns (u[nsys, n], a[nsys], f, g[n]).
+    """
+    n = int(np.prod(shape))
+    A = helmholtz_matrix(shape, h, omega, m, npml, v_max, R)
+    w = stretch_weight(shape, h, omega, npml, v_max, R)
+    lu = spla.splu(A.tocsc())
+    us, als = [], []
+    f = 0.0
+    g = np.zeros(n)
+    for s in range(len(srcs)):
+        rec = np.asarray(rec_idx[rec_off[s]:rec_off[s + 1]], dtype=np.int64)
+        ds = np.asarray(d[rec_off[s]:rec_off[s + 1]], dtype=np.complex128)
+        Ge = lu.solve(unit_vector(n, srcs[s]))
+        PG = Ge[rec]
+        a = (np.vdot(PG, ds) / np.vdot(PG, PG)) if alpha is None else complex(alpha[s])
+        u = a * Ge
+        r = u[rec] - ds
+        rhs_adj = np.zeros(n, dtype=np.complex128)
+        rhs_adj[rec] = r
+        v = lu.solve(rhs_adj, trans="H")
+        f += 0.5 * np.vdot(r, r).real
+        g += -omega ** 2 * np.real(w * u * np.conj(v))
         us.append(u)
         als.append(a)
     return np.array(us), np.array(als), f, g

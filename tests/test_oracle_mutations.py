@@ -16,6 +16,7 @@ import scipy.sparse as sp
 import oracle
 import oracle.awri_oracle as AW
 import oracle.wri_oracle as W
+import test_oracle_fwi as F
 import test_oracle_pins as P
 
 
@@ -102,6 +103,15 @@ MUTATIONS = [
     ("l-BFGS: pairs taken newest first", AW, "two_loop",
      lambda o: (lambda g, S, Y, h0=None: o(g, S[::-1], Y[::-1], h0)),
      P.test_two_loop_recursion_equals_dense_bfgs_inverse, {}),
+    ("reduced FWI: gradient sign", W, "fwi_evaluate",
+     lambda o: (lambda *a, **k: (lambda u, al, f, g: (u, al, f, -g))(*o(*a, **k))),
+     F.test_fwi_gradient_matches_central_differences, {"source_free": True}),
+    ("reduced FWI: omega in place of omega^2", W, "fwi_evaluate",
+     lambda o: (lambda *a, **k: (lambda u, al, f, g: (u, al, f, g / a[2]))(*o(*a, **k))),
+     F.test_fwi_gradient_matches_central_differences, {"source_free": False}),
+    ("reduced FWI: stretch weight dropped from the gradient", W, "stretch_weight",
+     lambda o: (lambda *a, **k: np.ones_like(o(*a, **k))),
+     F.test_fwi_gradient_matches_central_differences, {"source_free": False}),
 ]
 
 
