@@ -26,8 +26,13 @@
  *     are ordinary host memory read before the call returns.  The library never
  *     allocates device memory: scratch comes from the caller's workspace.
  *   - Every call enqueues its work on `stream` (a cudaStream_t; 0 is the legacy
- *     default stream).  wri_solve_batch additionally waits on the host for the
- *     stopping decision (it polls a device counter every few iterations).
+ *     default stream).  wri_solve_batch additionally waits on the host for the end of
+ *     the solve: the CG iterations loop on the device (a CUDA-graph WHILE node that a
+ *     small control kernel keeps going while systems remain), and the host reads the
+ *     device counters once per inner solve to return an error code.
+ *   - Calls from different host threads may run at the same time on different streams
+ *     with different workspaces (per-thread host read-back buffers, a mutex around the
+ *     shared graph cache); wri_gradient_noalloc is the exception (see there).
  *   - Return value: WRI_OK or an error code (wri_strerror).  Argument errors are
  *     detected before any work is enqueued.  Per-system outcomes go to device arrays.
  */
@@ -108,13 +113,15 @@ typedef struct {
   int32_t dtype;       /* WRI_C64 or WRI_C128 */
   int32_t warm_start;  /* 1: start from the values in u; 0: start from u = 0 */
   int32_t max_refine;  /* WRI_C64 only: > 0 enables FP64 iterative refinement, at most this
-                          many outer corrections; each inner FP32 solve runs to inner_tol */
+                          many outer corrections; each inner FP32 solve runs to inner_tol, or to
+                          the looser tolerance that already meets refine_tol with 20 % of margin
+                          (a cold start's first inner solve: max(inner_tol, 0.8 refine_tol)) */
   double refine_tol;   /* refinement stops when the FP64 relative residual <= refine_tol */
   double inner_tol;    /* relative tolerance of each inner FP32 solve (e.g. 1e-3) */
   int32_t plain;       /* 1: unbatched, unfused baseline (one system at a time, separate
                           BLAS-1 kernels, scalars read back by the host every iteration) */
-  int32_t poll_every;  /* iterations launched between host polls of the done-counter
-                          (0 = library default) */
+  int32_t poll_every;  /* CG iterations per body of the device-side loop, between two runs of
+                          its control kernel (0 = library default, about 300 us of work) */
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
   int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
@@ -128,6 +135,11 @@ typedef struct {
   int32_t wait_limit_us; /* TMA phases: time limit of every wait of the copy pipelines, in
                             microseconds (0 = 2 s).  A wait that runs out stops the solve:
                             wri_solve_batch returns WRI_ECUDA and the context stays usable. */
+  int32_t host_loop;     /* 1: the host replays a graph of poll_every iterations and reads the
+                            counters after each replay, instead of the device-side loop (a graph
+                            WHILE node).  Kernel profilers cannot see kernels inside conditional
+                            graph nodes; this keeps the phase kernels visible to them.  The
+                            environment variable WRI_HOST_LOOP=1 sets it for every solve. */
   int32_t test_withhold; /* test hook of the bounded waits, 0 = off.  k > 0: in the warp-specialised
                             TMA phases the copy warp of block 0 never issues its (k-1)-th plane
                             fill, so the wait for it runs out after wait_limit_us.  Nothing

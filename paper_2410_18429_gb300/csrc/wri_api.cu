@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -110,10 +111,25 @@ void decompose(const wri_grid& g, int by, int zs_req, GroupDev& G) {
   G.ntiles = G.tiles_x * G.tiles_y * G.zsplit;
 }
 
-int auto_zsplit(long long xy_items) {
-  int zs = 1;
-  while (xy_items * zs < 8LL * kRefSMs && zs < 16) zs *= 2;
-  return zs;
+// z-chunks per tile column when the caller leaves it open: the count that minimises the modelled
+// time of one launch, the waves of resident CTAs (items / (152 SMs x 4 CTAs), rounded up) times the
+// planes each item streams (its chunk plus the two halo planes), over 1..16 chunks of >= 4 planes.
+// Large batches keep whole columns (one chunk); a single system of a 148^3 grid gets 6 chunks of 25
+// planes, one wave of 570 items.
+int auto_zsplit(long long xy_items, int nz) {
+  const long long wave = (long long)kRefSMs * 4;
+  int best = 1;
+  double best_cost = 0.0;
+  for (int zs = 1; zs <= 16 && zs <= std::max(1, nz / 4); ++zs) {
+    const int zc = (nz + zs - 1) / zs;
+    const long long items = xy_items * ((nz + zc - 1) / zc);
+    const double cost = (double)((items + wave - 1) / wave) * (zc + 2);
+    if (zs == 1 || cost < best_cost) {
+      best_cost = cost;
+      best = zs;
+    }
+  }
+  return best;
 }
 
 int validate_groups(const wri_group* groups, int ngroups, bool need_data) {
@@ -146,6 +162,7 @@ int validate_groups(const wri_group* groups, int ngroups, bool need_data) {
 struct Plan {
   int ngroups = 0, nsys_total = 0, nnz_total = 0, dtype = 0, ir = 0, by = 8;
   int tma_cfg = -1;  // TMA configuration of the CG phases, -1 = z-march kernels
+  bool host_loop = false;  // the host replays the iteration graph (no conditional node)
   int vbytes = 8;   // bytes of one complex of the iteration vectors
   int rlbytes = 8;  // bytes of one complex of lamd / r2
   long long nitems = 0;
@@ -156,7 +173,7 @@ struct Plan {
   GroupDev g[WRI_MAXG];
   size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][2], v_s[WRI_MAXG], v_t1[WRI_MAXG];
   size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG], v_q64[WRI_MAXG], v_g32[WRI_MAXG], v_rmap[WRI_MAXG];
-  size_t off_ztab[WRI_MAXG];
+  size_t off_ztab[WRI_MAXG], off_ztab64[WRI_MAXG];  // z-coefficient tables (FP32, FP64) per group
   size_t off_rmask[WRI_MAXG], off_rcol[WRI_MAXG], rmask_bytes[WRI_MAXG], rcol_bytes[WRI_MAXG];
   std::vector<int> rec_base;  // first receiver entry of every group
 };
@@ -176,13 +193,28 @@ void plan_aux(const wri_group* groups, int ngroups, Plan& P) {
   off += align_up(sizeof(SysDev) * (size_t)P.nsys_total);
   P.off_rec = off;
   off += align_up(sizeof(int) * (size_t)std::max(P.nnz_total, 1));
+  for (int gi = 0; gi < ngroups; ++gi) {  // [2][nz][3] complex coefficients in FP32 and FP64
+    P.off_ztab[gi] = off;
+    off += align_up(sizeof(float) * 2 * 2 * 3 * (size_t)groups[gi].grid.nz);
+    P.off_ztab64[gi] = off;
+    off += align_up(sizeof(double) * 2 * 2 * 3 * (size_t)groups[gi].grid.nz);
+  }
   P.aux_total = off;
   P.total = off;
+}
+
+bool host_loop_forced() {
+  static const bool forced = [] {
+    const char* v = std::getenv("WRI_HOST_LOOP");
+    return v && v[0] == '1';
+  }();
+  return forced;
 }
 
 void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, Plan& P) {
   plan_aux(groups, ngroups, P);
   P.dtype = o->dtype;
+  P.host_loop = o->host_loop != 0 || host_loop_forced();
   P.ir = (o->dtype == WRI_C64 && o->max_refine > 0) ? 1 : 0;
   P.by = by_of_tile(o->tile);
   P.tma_cfg = -1;
@@ -205,7 +237,10 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
     const wri_grid& g = groups[gi].grid;
     xy_items += (long long)groups[gi].nsys * ((g.nx + WRI_TX - 1) / WRI_TX) * ((g.ny + P.by - 1) / P.by);
   }
-  const int zs = o->zsplit > 0 ? o->zsplit : auto_zsplit(o->plain ? xy_items / std::max(1, P.nsys_total) : xy_items);
+  int nz_max = 0;
+  for (int gi = 0; gi < ngroups; ++gi) nz_max = std::max(nz_max, groups[gi].grid.nz);
+  const int zs = o->zsplit > 0 ? o->zsplit
+                               : auto_zsplit(o->plain ? xy_items / std::max(1, P.nsys_total) : xy_items, nz_max);
   long long item = 0, parts = 0;
   int sys0 = 0;
   for (int gi = 0; gi < ngroups; ++gi) {
@@ -238,10 +273,6 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
     off += align_up(16 * (size_t)std::max(P.nnz_total, 1));
     P.off_r2_in = off;
     off += align_up(8 * (size_t)std::max(P.nnz_total, 1));
-  }
-  for (int gi = 0; gi < ngroups; ++gi) {
-    P.off_ztab[gi] = off;
-    off += align_up(sizeof(float) * 2 * 2 * 3 * (size_t)groups[gi].grid.nz);
   }
   for (int gi = 0; gi < ngroups; ++gi) {  // receiver bitmaps (one bit per node and system)
     const GroupDev& G = P.g[gi];
@@ -282,7 +313,7 @@ int validate_opts(const wri_solve_opts* o) {
   if (o->kernel < 0 || o->kernel > 1 + tma_config_count()) return WRI_EINVAL;
   if (o->order < 0 || o->order > 6) return WRI_EINVAL;
   if (o->l2_promotion < 0 || o->l2_promotion > 4) return WRI_EINVAL;
-  if (o->wait_limit_us < 0 || o->test_withhold < 0) return WRI_EINVAL;
+  if (o->wait_limit_us < 0 || o->test_withhold < 0 || o->host_loop < 0 || o->host_loop > 1) return WRI_EINVAL;
   if (o->max_refine > 0) {
     if (o->dtype != WRI_C64) return WRI_ENOTSUP;
     if (!(o->refine_tol >= 0) || !(o->inner_tol > 0 && o->inner_tol < 1)) return WRI_EINVAL;
@@ -421,6 +452,7 @@ Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_
     G.q64 = P.ir ? ws + P.v_q64[gi] : nullptr;
     G.gvec = (P.ir && inner_view) ? ws + P.v_g32[gi] : nullptr;
     G.ztab = (const float2*)(ws + P.off_ztab[gi]);
+    G.ztab64 = (const double2*)(ws + P.off_ztab64[gi]);
     G.rmask = (const uint32_t*)(ws + P.off_rmask[gi]);
     G.rcol = (const uint32_t*)(ws + P.off_rcol[gi]);
     b.g[gi] = G;
@@ -558,7 +590,7 @@ int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, 
   if (!c || !slot) return WRI_ECUDA;
   const int rb = P.ir ? 4 : P.vbytes / 2;
   const bool use_tma = tma && P.tma_cfg >= 0 && mode2 == M_P2;
-  const bool dev_loop = device_loop_supported();
+  const bool dev_loop = !P.host_loop && device_loop_supported();
   // loop bodies after which the device loop gives up: every system stops by max_iter + 1 iterations
   const int cap_bodies = (max_iter + 2 + K - 1) / K + 2;
   // graph lookup / capture
@@ -659,6 +691,7 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   b.tol = o->tol;
   const int vb = P.vbytes / 2;
   if (setup_rmask(P, b, ws, st) != WRI_OK) return WRI_ECUDA;
+  WRI_CK(launch_ztable(b, st));
   WRI_CK(launch_setup_rhs(o->dtype == WRI_C128 ? 8 : 4, vb, b, P.nsys_total, st));
   WRI_CK(cudaMemsetAsync(b.remaining, 0, 3 * sizeof(int), st));
   if (o->warm_start) {
@@ -681,7 +714,6 @@ int solve_fused(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
   b1.sblock = b2.sblock = (ord >= 4) ? (1 << (ord - 2)) : 1;  // 4 -> 4 systems, 5 -> 8, 6 -> 16
   const int K = o->poll_every > 0 ? o->poll_every : poll_default(P);
   if (P.tma_cfg >= 0) {
-    WRI_CK(launch_ztable(b, st));
     static thread_local TmaSet T;  // ~8 KB: kept off the stack
     if (build_tma(b, P, b.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, o, T))
       return run_loop(P, b1, b2, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, &T);
@@ -720,6 +752,7 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
   Batch inner = solver_batch(groups, P, ws, true);
   inner.max_iter = o->max_iter;
   if (setup_rmask(P, inner, ws, st) != WRI_OK) return WRI_ECUDA;
+  WRI_CK(launch_ztable(inner, st));  // the outer view shares the tables
   void* u[WRI_MAXG] = {};
   for (int gi = 0; gi < P.ngroups; ++gi) u[gi] = groups[gi].u;
   // lambda d in FP64 (lamd and q2), x64 = warm ? u : 0, r64 = 0, dx = 0
@@ -746,11 +779,32 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
     const int ord = o->order ? o->order : kDefaultOrder;
     inner.order = (ord == 1) ? 1 : (ord == 3) ? 2 : (ord >= 4) ? 3 : 0;
     inner.sblock = (ord >= 4) ? (1 << (ord - 2)) : 1;
-    WRI_CK(launch_ztable(inner, st));
     if (build_tma(inner, P, inner.remaining + 1, o->l2_promotion ? o->l2_promotion : kDefaultPromotion, o, T))
       tma = &T;
   }
-  for (int outer_k = 0;; ++outer_k) {
+  int first_outer = 0;
+  if (!o->warm_start) {
+    // Cold start: x64 = 0 and r64 = 0, so the first outer step's residual is b itself and needs no
+    // FP64 pass.  The first inner solve starts like an unrefined solve, from r = b (the point field
+    // b1 and lambda d) and s = S^H b formed in FP32; ||S^H b|| is the reference of every outer test.
+    WRI_CK(launch_ir_cold(inner, P.nsys_total, st));               // r2_in = lambda d (complex64)
+    WRI_CK(cudaMemsetAsync(inner.remaining, 0, 3 * sizeof(int), st));
+    Batch r = inner;
+    r.flavor = SH_INIT;
+    r.tol = std::max(o->inner_tol, 0.8 * o->refine_tol);
+    WRI_CK(march(4, 4, M_SH, true, P.by, r, st));                  // s = S^H b, r1 = b1, dx = 0
+    WRI_CK(cudaMemcpyAsync(slot, inner.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WRI_CK(cudaStreamSynchronize(st));
+    if (*slot > 0) {
+      Batch in = inner;
+      for (int gi = 0; gi < P.ngroups; ++gi) in.g[gi].gvec = nullptr;  // r64 = 0: no g'
+      const int rc = run_loop(P, in, in, M_P2, std::min(K, o->max_iter + 1), o->max_iter, st, tma);
+      if (rc != WRI_OK) return rc;
+      WRI_CK(launch_ir_update(inner, st));                         // x64 = dx, r64 = dr
+    }
+    first_outer = 1;
+  }
+  for (int outer_k = first_outer;; ++outer_k) {
     WRI_CK(cudaMemsetAsync(outer.remaining, 0, 3 * sizeof(int), st));
     Batch r = outer;
     r.outer = outer_k;
@@ -802,7 +856,8 @@ int solve_plain(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
     G1.masked = U.alpha ? 0 : 1;
     G1.m = U.m;
     G1.m_double = P.dtype == WRI_C128 ? 1 : 0;
-    decompose(U.grid, P.by, o->zsplit > 0 ? o->zsplit : auto_zsplit((long long)G1.tiles_x * G1.tiles_y), G1);
+    decompose(U.grid, P.by, o->zsplit > 0 ? o->zsplit : auto_zsplit((long long)G1.tiles_x * G1.tiles_y, U.grid.nz),
+              G1);
     G1.nsys = 1;
     G1.sys0 = 0;
     G1.item0 = 0;
@@ -923,7 +978,8 @@ int apply_common(const wri_grid* grid, int dtype, const void* m, int nsys, const
   b.by = 8;
   GroupDev& G = b.g[0];
   fill_geom(G, *grid);
-  decompose(*grid, 8, auto_zsplit((long long)nsys * ((grid->nx + WRI_TX - 1) / WRI_TX) * ((grid->ny + 7) / 8)), G);
+  decompose(*grid, 8, auto_zsplit((long long)nsys * ((grid->nx + WRI_TX - 1) / WRI_TX) * ((grid->ny + 7) / 8), grid->nz),
+            G);
   G.nsys = nsys;
   G.item0 = 0;
   G.nitems = (long long)G.ntiles * nsys;
@@ -976,6 +1032,8 @@ Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, i
     G.m_double = dtype == WRI_C128 ? 1 : 0;
     G.d = groups[gi].d;
     G.x = wide ? groups[gi].u64 : groups[gi].u;
+    G.ztab = (const float2*)(ws + P.off_ztab[gi]);
+    G.ztab64 = (const double2*)(ws + P.off_ztab64[gi]);
     // gradient decomposition: one work item per tile, systems looped inside
     G.tiles_x = (G.nx + WRI_TX - 1) / WRI_TX;
     G.tiles_y = (G.ny + 7) / 8;
@@ -1043,6 +1101,7 @@ int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype, const 
     b.g[gi].grad = grad[gi];
   }
   const int rb = (dtype == WRI_C128 || wide) ? 8 : 4;
+  WRI_CK(launch_ztable(b, st));
   WRI_CK(march(rb, rb, M_GRAD, false, 8, b, st));
   WRI_CK(launch_data_term(rb, dtype == WRI_C128 ? 8 : 4, b, P.nsys_total, st));
   return WRI_OK;
@@ -1158,6 +1217,7 @@ int wri_gradient(const wri_group* groups, int ngroups, int dtype, const double* 
     b.g[gi].grad = grad[gi];
   }
   const int rb = (dtype == WRI_C128 || wide) ? 8 : 4;
+  WRI_CK(launch_ztable(b, st));
   WRI_CK(march(rb, rb, M_GRAD, false, 8, b, st));
   WRI_CK(launch_data_term(rb, dtype == WRI_C128 ? 8 : 4, b, P.nsys_total, st));
   return WRI_OK;

@@ -156,7 +156,8 @@ struct GroupDev {
   const uint32_t* rcol;     // [nsys][ny][tiles_x] OR of rmask over k (columns holding a receiver)
   double* grad;             // [n] gradient accumulator (gradient kernel only)
   const float2* ztab;       // [2][nz][3] z-axis coefficients (s_z, 1/(s_z(k-1/2) h^2), 1/(s_z(k+1/2) h^2)),
-                            // [0] for A, [1] conjugated for A^H; FP32, built once per solve
+                            // [0] for A, [1] conjugated for A^H; FP32, built once per call (or null)
+  const double2* ztab64;    // the same table in FP64 (the z-march FP64 kernels), or null
 };
 
 struct Batch {

@@ -26,6 +26,7 @@ cudaError_t launch_export(const SysDev* sys, int nsys, int32_t* iters, double* r
 // FP64 refinement (b: inner complex64 view; u: the caller's wavefields, one per group)
 cudaError_t launch_ir_init(const Batch& b, void* const* u, int warm, cudaStream_t st);
 cudaError_t launch_ir_rmap(const Batch& b, int nsys_total, cudaStream_t st);  // b: outer view, map filled with -1
+cudaError_t launch_ir_cold(const Batch& b, int nsys_total, cudaStream_t st);  // b: inner view
 cudaError_t launch_ir_forcing(const Batch& b, const void* q2, cudaStream_t st);
 cudaError_t launch_ir_update(const Batch& b, cudaStream_t st);
 cudaError_t launch_ir_final(const Batch& b, void* const* u, cudaStream_t st);

@@ -102,6 +102,23 @@ __device__ __forceinline__ ZCoef<R> z_coef(const GroupDev& G, int k) {
   return c;
 }
 
+// z-axis coefficients of plane k from the per-call table (no FP64 division per node-plane on the
+// narrow FP64 pipe), or computed when the call built no table.
+__device__ __forceinline__ const float2* ztab_of(const GroupDev& G, float) { return G.ztab; }
+__device__ __forceinline__ const double2* ztab_of(const GroupDev& G, double) { return G.ztab64; }
+
+template <typename R, bool CONJ>
+__device__ __forceinline__ ZCoef<R> z_lookup(const GroupDev& G, int k) {
+  const cx<R>* t = ztab_of(G, R(0));
+  if (!t) return z_coef<R, CONJ>(G, k);
+  t += (CONJ ? 3 * G.nz : 0) + 3 * k;
+  ZCoef<R> c;
+  c.sz = __ldg(t);
+  c.izm = __ldg(t + 1);
+  c.izp = __ldg(t + 2);
+  return c;
+}
+
 // Receiver nodes in the normal-residual norms ||S^H r||^2.  At a receiver node of system sl the
 // finalizer adds lambda P^T r2 to the stencil value A^H r1 and accounts |s|^2 of the sum itself,
 // so the stencil passes leave those nodes out of their partial sums.  (Summing |A^H r1|^2 over
@@ -147,27 +164,47 @@ __device__ __forceinline__ cx<R> stencil_general(const GroupDev& G, const XYCoef
 // s = 1 and real coefficients 1/h^2.  Same value as stencil_general, written as
 //   A u = s_z (s_y Lx + s_x Ly) + s_x s_y (Lz + omega^2 m s_z u),
 //   L_a = c_a(+1/2) (u_next - u) - c_a(-1/2) (u - u_prev),  c_a = 1/(s_a(half) h^2).
-template <bool XP, bool YP, bool ZP>
-__device__ __forceinline__ float2 stencil_axes(float ih2, float om2m, float2 u, float2 uxm, float2 uxp, float2 uym,
-                                               float2 uyp, float2 uzm, float2 uzp, float2 sx, float2 ixm,
-                                               float2 ixp, float2 sy, float2 iym, float2 iyp, float2 sz,
-                                               float2 izm, float2 izp) {
-  float2 lx, ly, lz;
+template <bool XP, bool YP, bool ZP, typename R>
+__device__ __forceinline__ cx<R> stencil_axes(R ih2, R om2m, cx<R> u, cx<R> uxm, cx<R> uxp, cx<R> uym, cx<R> uyp,
+                                              cx<R> uzm, cx<R> uzp, cx<R> sx, cx<R> ixm, cx<R> ixp, cx<R> sy,
+                                              cx<R> iym, cx<R> iyp, cx<R> sz, cx<R> izm, cx<R> izp) {
+  cx<R> lx, ly, lz;
   if (XP) lx = ixp * (uxp - u) - ixm * (u - uxm);
-  else lx = ih2 * ((uxp + uxm) - 2.f * u);
+  else lx = ih2 * ((uxp + uxm) - R(2) * u);
   if (YP) ly = iyp * (uyp - u) - iym * (u - uym);
-  else ly = ih2 * ((uyp + uym) - 2.f * u);
+  else ly = ih2 * ((uyp + uym) - R(2) * u);
   if (ZP) lz = izp * (uzp - u) - izm * (u - uzm);
-  else lz = ih2 * ((uzp + uzm) - 2.f * u);
-  const float2 a = (YP ? sy * lx : lx) + (XP ? sx * ly : ly);
-  const float2 zu = ZP ? sz * u : u;
-  const float2 b = lz + om2m * zu;
-  const float2 za = ZP ? sz * a : a;
-  float2 bb = b;
+  else lz = ih2 * ((uzp + uzm) - R(2) * u);
+  const cx<R> a = (YP ? sy * lx : lx) + (XP ? sx * ly : ly);
+  const cx<R> zu = ZP ? sz * u : u;
+  const cx<R> b = lz + om2m * zu;
+  const cx<R> za = ZP ? sz * a : a;
+  cx<R> bb = b;
   if (XP && YP) bb = (sx * sy) * b;
   else if (XP) bb = sx * b;
   else if (YP) bb = sy * b;
   return za + bb;
+}
+
+// Dispatch of stencil_axes on the stretched axes var = 4 x + 2 y + z (var = 0: every factor is
+// 1, the plain 7-point formula).
+template <typename R>
+__device__ __forceinline__ cx<R> stencil_var(int var, R ih2, R om2m, cx<R> u, cx<R> uxm, cx<R> uxp, cx<R> uym,
+                                             cx<R> uyp, cx<R> uzm, cx<R> uzp, const XYCoef<R>& c, const ZCoef<R>& z) {
+#define WRI_VAR(X_, Y_, Z_) \
+  return stencil_axes<X_, Y_, Z_>(ih2, om2m, u, uxm, uxp, uym, uyp, uzm, uzp, c.sx, c.ixm, c.ixp, c.sy, c.iym, c.iyp, \
+                                  z.sz, z.izm, z.izp);
+  switch (var) {
+    case 1: WRI_VAR(false, false, true)
+    case 2: WRI_VAR(false, true, false)
+    case 3: WRI_VAR(false, true, true)
+    case 4: WRI_VAR(true, false, false)
+    case 5: WRI_VAR(true, false, true)
+    case 6: WRI_VAR(true, true, false)
+    case 7: WRI_VAR(true, true, true)
+    default: WRI_VAR(false, false, false)
+  }
+#undef WRI_VAR
 }
 
 // (A u) at one node in the interior (all stretch factors 1): omega^2 m u + Laplacian.

@@ -159,7 +159,9 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
           sd->status = WRI_SYS_OK;
           sd->gamma = g;
           sd->snorm_ref = rn;
-          sd->tol = b.inner_tol;
+          // the correction needs no more accuracy than the outer target asks for (20 % of
+          // margin): an inner tolerance tighter than that would only add iterations
+          sd->tol = fmax(b.inner_tol, 0.8 * b.refine_tol * sd->snorm_b / rn);
           sd->beta = 0.0;
           sd->alpha = 0.0;
           sd->iter = 0;
@@ -259,8 +261,9 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
       interior_range(G.ax, xlo, xhi);
       interior_range(G.ay, ylo, yhi);
       interior_range(G.az, zlo, zhi);
-      const bool xy_int = (x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi) && (y0 >= ylo) &&
-                          (min(y0 + BY, ny) - 1 <= yhi);
+      // stretched axes of this tile (bit 2: x, bit 1: y); bit 0 (z) is set per plane
+      const int xyvar = (((x0 >= xlo) && (min(x0 + WRI_TX, nx) - 1 <= xhi)) ? 0 : 4) |
+                        (((y0 >= ylo) && (min(y0 + BY, ny) - 1 <= yhi)) ? 0 : 2);
       const R om2 = pick<R>(G.omega * G.omega, G.om2f);
       const R ih2 = inv_h2<R>(G);
 
@@ -379,12 +382,14 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
           const R om2m = own ? om2 * model_at<R>(G.m, G.m_double, node) : R(0);
           C AF;
           ZCoef<R> zc;
-          const bool fast = xy_int && (k >= zlo) && (k <= zhi);
+          const int var = xyvar | ((k >= zlo && k <= zhi) ? 0 : 1);
+          const bool fast = var == 0;
           if (fast) {
             AF = stencil_interior<R>(ih2, om2m, u, uxm, uxp, uym, uyp, Fm, Fp);
           } else {
-            zc = z_coef<R, CONJ>(G, k);
-            AF = stencil_general<R, CONJ>(G, cxy, zc, om2m, u, uxm, uxp, uym, uyp, Fm, Fp);
+            // only the stretched axes take complex coefficients (stencil_axes)
+            zc = z_lookup<R, CONJ>(G, k);
+            AF = stencil_var<R>(var, ih2, om2m, u, uxm, uxp, uym, uyp, Fm, Fp, cxy, zc);
           }
           if (own) {
             const long long gnode = off + node;

@@ -60,6 +60,12 @@ cudaError_t launch_ir_rmap(const Batch& b, int nsys_total, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_ir_cold(const Batch& b, int nsys_total, cudaStream_t st) {
+  if (nsys_total <= 0) return cudaSuccess;
+  k_ir_cold<<<nsys_total, 128, 0, st>>>(b, nsys_total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ir_forcing(const Batch& b, const void* q2, cudaStream_t st) {
   k_ir_forcing<<<1024, 256, 0, st>>>(b, (const double2*)q2);
   return cudaGetLastError();

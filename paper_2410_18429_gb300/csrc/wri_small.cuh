@@ -59,22 +59,29 @@ __global__ void k_loop_ctl(cudaGraphConditionalHandle h, int* counters, int cap)
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-// z-axis coefficient tables of every group (FP32): one thread per (group, plane).
+// z-axis coefficient tables of every group (FP32 and FP64, where the batch has them): one thread
+// per (group, plane).
+template <typename R>
+__device__ __forceinline__ void ztable_fill(const GroupDev& G, cx<R>* t, int k) {
+  const ZCoef<R> a = z_coef<R, false>(G, k);
+  const ZCoef<R> h = z_coef<R, true>(G, k);
+  t[3 * k + 0] = a.sz;
+  t[3 * k + 1] = a.izm;
+  t[3 * k + 2] = a.izp;
+  t[3 * (G.nz + k) + 0] = h.sz;
+  t[3 * (G.nz + k) + 1] = h.izm;
+  t[3 * (G.nz + k) + 2] = h.izp;
+}
+
 __global__ void k_ztable(const __grid_constant__ Batch b) {
   const int g = blockIdx.y;
   if (g >= b.ngroups) return;
   const GroupDev& G = b.g[g];
   float2* t = const_cast<float2*>(G.ztab);
-  if (!t) return;
+  double2* t64 = const_cast<double2*>(G.ztab64);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.nz; k += gridDim.x * blockDim.x) {
-    const ZCoef<float> a = z_coef<float, false>(G, k);
-    const ZCoef<float> h = z_coef<float, true>(G, k);
-    t[3 * k + 0] = a.sz;
-    t[3 * k + 1] = a.izm;
-    t[3 * k + 2] = a.izp;
-    t[3 * (G.nz + k) + 0] = h.sz;
-    t[3 * (G.nz + k) + 1] = h.izm;
-    t[3 * (G.nz + k) + 2] = h.izp;
+    if (t) ztable_fill<float>(G, t, k);
+    if (t64) ztable_fill<double>(G, t64, k);
   }
 }
 
@@ -133,6 +140,17 @@ __global__ void k_ir_init(const __grid_constant__ Batch b, IrU U, int warm) {
   double2* r2 = (double2*)b.r2_64;
   for (int s = blockIdx.x; s < ns; s += gridDim.x)
     for (int k = b.sys[s].rec_begin + threadIdx.x; k < b.sys[s].rec_end; k += blockDim.x) r2[k] = make_double2(0.0, 0.0);
+}
+
+// Cold start of the refinement (x64 = 0, r64 = 0, so b - S x64 = b): the first inner solve's
+// receiver residual is lambda d, rounded to complex64.  b: the inner view (r2 = r2_in, lamd FP64).
+__global__ void k_ir_cold(const __grid_constant__ Batch b, int nsys_total) {
+  const int s = blockIdx.x;
+  if (s >= nsys_total) return;
+  const double2* lamd = (const double2*)b.lamd;
+  float2* r2 = (float2*)b.r2;
+  for (int k = b.sys[s].rec_begin + threadIdx.x; k < b.sys[s].rec_end; k += blockDim.x)
+    r2[k] = make_float2((float)lamd[k].x, (float)lamd[k].y);
 }
 
 // Forcing of an outer step: inner r1[0] = q64 - r64 (= f on the nodes) and inner receiver

@@ -40,7 +40,8 @@ class WriSolveOpts(C.Structure):
                 ("warm_start", C.c_int32), ("max_refine", C.c_int32), ("refine_tol", C.c_double),
                 ("inner_tol", C.c_double), ("plain", C.c_int32), ("poll_every", C.c_int32),
                 ("tile", C.c_int32), ("zsplit", C.c_int32), ("kernel", C.c_int32), ("order", C.c_int32),
-                ("l2_promotion", C.c_int32), ("wait_limit_us", C.c_int32), ("test_withhold", C.c_int32)]
+                ("l2_promotion", C.c_int32), ("wait_limit_us", C.c_int32), ("host_loop", C.c_int32),
+                ("test_withhold", C.c_int32)]
 
 
 class WriError(RuntimeError):
@@ -221,11 +222,11 @@ def KERNEL_TMA(cfg: int = 0) -> int:
 
 def make_opts(tol=1e-6, max_iter=10000, dtype=C64, warm_start=False, max_refine=0, refine_tol=1e-10,
               inner_tol=1e-3, plain=False, poll_every=0, tile=0, zsplit=0, kernel=KERNEL_AUTO,
-              order=0, l2_promotion=0, wait_limit_us=0, test_withhold=0) -> WriSolveOpts:
+              order=0, l2_promotion=0, wait_limit_us=0, host_loop=False, test_withhold=0) -> WriSolveOpts:
     return WriSolveOpts(float(tol), int(max_iter), int(dtype), int(bool(warm_start)), int(max_refine),
                         float(refine_tol), float(inner_tol), int(bool(plain)), int(poll_every), int(tile),
                         int(zsplit), int(kernel), int(order), int(l2_promotion), int(wait_limit_us),
-                        int(test_withhold))
+                        int(bool(host_loop)), int(test_withhold))
 
 
 def workspace_size(groups: Sequence[GroupSpec], opts: WriSolveOpts) -> int:

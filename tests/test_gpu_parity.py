@@ -515,6 +515,22 @@ def test_max_iter_one_and_status(W):
         W.solve([spec], W.make_opts(tol=-1.0, dtype=0))
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_host_loop_equals_device_loop(W, kernel):
+    """The host-replayed iteration graph (host_loop, kept for kernel profilers) and the device-side
+    WHILE loop run the same kernels in the same order: bit-identical iterates and residuals, on a
+    converged solve (tol 1e-4, so the loop's stopping decision is exercised) and a fixed budget."""
+    G = case(nphys=(36, 13, 10), npml=4, nsys=3)
+    for tol, k in ((1e-4, 100000), (0.0, 30)):
+        out = []
+        for host in (False, True):
+            sp = _spec(W, G, 0)
+            it, rr, st = W.solve([sp], W.make_opts(tol=tol, max_iter=k, dtype=0, kernel=kernel, host_loop=host))
+            out.append((sp.u.clone(), it.clone(), rr.clone(), st.clone()))
+        assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+        assert torch.equal(out[0][2], out[1][2]) and torch.equal(out[0][3], out[1][3])
+
+
 @pytest.mark.parametrize("cfg", [9, 18])
 def test_copy_wait_time_out_is_reported_and_the_context_recovers(W, cfg):
     """Bounded waits of the warp-specialised TMA phases.  With the test hook the copy warp of block
