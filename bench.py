@@ -311,17 +311,18 @@ def solve_opts(wri, args, certified=True, iters=None, **kw):
     return wri.make_opts(**base)
 
 
-def step_launches(iters, k, certified):
+def step_launches(iters, k, certified, ngroups):
     """Kernels of libwri in one step (the claim of the bench line).  Both configurations: the
-    receiver bitmaps, the right-hand sides, the z tables, the loop of phase 1 + phase 2 in bodies
-    of K iterations with one control kernel each (the P1 after the last iteration is the x-only
-    pass), the export, the source estimate, the gradient and the data term.  Refinement adds the
-    receiver map, its init, two FP64 residual steps of 3 kernels (residual, forcing, S^H), the
-    update and the final rounding; without it the initial S^H b is one kernel."""
+    receiver bitmaps, the z tables, the right-hand sides, the initial S^H b, the loop of phase 1 +
+    phase 2 in bodies of K iterations with one control kernel each (the P1 after the last iteration
+    is the x-only pass), the export and the source estimate.  Certified: the refinement's receiver
+    map, init and cold start (r2), its update, one FP64 residual step of 3 kernels (residual,
+    forcing, S^H), the final rounding, and the gradient from that residual (one kernel per group).
+    Unrefined: the gradient's z tables, gradient kernel and data term."""
     bodies = -(-(iters + 1) // k)
     loop = bodies * (2 * k + 1)
-    fixed = 3 + 4
-    fixed += (1 + 1 + 3 + 1 + 3 + 1) if certified else 1
+    fixed = 1 + 1 + 1 + 1 + 1 + 1
+    fixed += (1 + 1 + 1 + 1 + 3 + 1 + ngroups) if certified else 3
     return loop + fixed
 
 
@@ -334,6 +335,33 @@ def subset(groups, per_group):
         out.append(synth.Group(g.spec, g.freq, g.v, g.src[:k], g.rec_off[:k + 1] - g.rec_off[0],
                                g.rec_idx[g.rec_off[0]:g.rec_off[k]], g.lam, g.v_max, g.pml_R, g.alpha[:k],
                                g.d[g.rec_off[0]:g.rec_off[k]]))
+    return out
+
+
+def true_relres(wri, grp, u64, dev):
+    """||S^H (b - S u)|| / ||S^H b|| of every system of a group in FP64, for FP64 wavefields u64
+    [nsys, n], with the complex128 operator of libwri on the float32 model and complex64 data the
+    complex64 solves saw (a measurement of the bench: the vector arithmetic around the two operator
+    applications is torch's).  Source-free mode."""
+    import numpy as np
+    import torch
+    from paper_2410_18429_gb300.problem import to_device
+    m32 = grp.m.astype(np.float32).astype(np.float64)
+    d32 = grp.d.astype(np.complex64).astype(np.complex128)
+    sp = to_device(grp, wri.C128, dev, m=m32, d=d32)
+    out = []
+    for s in range(grp.nsys):
+        us = u64[s:s + 1]
+        Au = wri.apply_A(sp, us)[0]
+        Au[int(grp.src[s])] = 0
+        rec = torch.as_tensor(grp.rec_idx[grp.rec_off[s]:grp.rec_off[s + 1]].astype(np.int64), device=dev)
+        d = torch.as_tensor(d32[grp.rec_off[s]:grp.rec_off[s + 1]], device=dev)
+        r2 = grp.lam * (d - us[0, rec])
+        sv = wri.apply_A(sp, (-Au)[None], adjoint=True)[0]
+        sv[rec] += grp.lam * r2
+        sb = torch.zeros_like(sv)
+        sb[rec] = grp.lam ** 2 * d
+        out.append(float(sv.norm() / sb.norm()))
     return out
 
 
@@ -381,6 +409,14 @@ def main():
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    def gradient_of_solve(sp, o, a, g_out, f_out, w):
+        """g and f of the wavefields the last solve left: from the refined solve's FP64 residual (no
+        stencil pass) in the certified configuration, else the gradient kernel on the wavefields."""
+        if int(o.max_refine) > 0 and all(s_.u64 is not None for s_ in sp):
+            wri.gradient_refined(sp, o, w, grads=g_out, f=f_out)
+        else:
+            wri.gradient(sp, wri.C64, a, grads=g_out, f=f_out, workspace=w)
+
     def step(sp, o, solve_events=None):
         if solve_events is not None:
             solve_events[0].record(stream)
@@ -391,7 +427,7 @@ def main():
         for g in grads:
             g.zero_()
         f.zero_()
-        wri.gradient(sp, wri.C64, a, grads=grads, f=f, workspace=work)
+        gradient_of_solve(sp, o, a, grads, f, work)
         if ws > 1:
             allreduce_gradient(grads, f)
         return it, rr, st
@@ -538,12 +574,14 @@ def main():
         tf = torch.zeros(1, dtype=torch.float64, device=dev)
 
         def grad_at_tol(sp, o, w):
+            if w is None:
+                w = torch.empty(wri.workspace_size(sp, o), dtype=torch.uint8, device=dev)
             it_, rr_, st_ = wri.solve(sp, o, workspace=w)
             a_ = wri.source_estimate(sp, wri.C64, workspace=w)
             for g in tgr[:len(sp)]:
                 g.zero_()
             tf.zero_()
-            wri.gradient(sp, wri.C64, a_, grads=tgr[:len(sp)], f=tf, workspace=w)
+            gradient_of_solve(sp, o, a_, tgr[:len(sp)], tf, w)
             return it_, rr_, st_
 
         tclk = Clocks(local)
@@ -575,9 +613,17 @@ def main():
 
         fsp = with_u64([to_device(g, wri.C64, dev) for g in one_groups], dev)
         (fit, _, fst), t_fused3 = timed_grad(fsp, tol_opts)
+        f_true = [true_relres(wri, g, sp_.u64, dev)[0] for g, sp_ in zip(one_groups, fsp)]
+        # the same stopping rule as the plain path: unrefined, the FP32 recurrence's residual decides
+        usp = with_u64([to_device(g, wri.C64, dev) for g in one_groups], dev)
+        u_opts = solve_opts(wri, args, certified=False, tol=1e-2, max_iter=200000, kernel=int(opts.kernel),
+                            order=int(opts.order))
+        (uit, _, ust), t_unref3 = timed_grad(usp, u_opts)
+        u_true = [true_relres(wri, g, sp_.u64, dev)[0] for g, sp_ in zip(one_groups, usp)]
         psp = with_u64([to_device(g, wri.C64, dev) for g in one_groups], dev)
         p_opts = wri.make_opts(tol=1e-2, max_iter=200000, dtype=wri.C64, plain=True)
         (pit, prr, pst), t_plain = timed_grad(psp, p_opts)
+        p_true = [true_relres(wri, g, sp_.u64, dev)[0] for g, sp_ in zip(one_groups, psp)]
         extras["at_tolerance"] = {
             "tol": 1e-2, "systems": nt, "sources_per_group": ntol, "measured": True,
             "ms_per_step": t_tol * 1e3, "value": nt / t_tol, "unit": UNIT,
@@ -586,14 +632,20 @@ def main():
             "status_all_ok": bool(int(st_t.max().item()) == wri.SYS_OK),
             "clocks": clk_tol,
             "same_systems": {
-                "systems": "the first source of every group (3 systems), one call each path, tol 1e-2",
-                "fused_ms": t_fused3 * 1e3, "fused_iters_per_group": [int(x) for x in fit.cpu().tolist()],
-                "fused_status_all_ok": bool(int(fst.max().item()) == wri.SYS_OK),
-                "plain_ms": t_plain * 1e3, "plain_iters_per_group": [int(x) for x in pit.cpu().tolist()],
-                "plain_status_all_ok": bool(int(pst.max().item()) == wri.SYS_OK),
-                "speedup_vs_plain": t_plain / t_fused3},
+                "systems": "the first source of every group (3 systems), one call per path, tol 1e-2; "
+                           "true_relres = ||S^H (b - S u)|| / ||S^H b|| of the returned wavefield in FP64",
+                "fused_unrefined": {"ms": t_unref3 * 1e3, "iters_per_group": [int(x) for x in uit.cpu().tolist()],
+                                    "status_all_ok": bool(int(ust.max().item()) == wri.SYS_OK),
+                                    "true_relres": u_true},
+                "plain": {"ms": t_plain * 1e3, "iters_per_group": [int(x) for x in pit.cpu().tolist()],
+                          "status_all_ok": bool(int(pst.max().item()) == wri.SYS_OK), "true_relres": p_true},
+                "fused_certified": {"ms": t_fused3 * 1e3, "iters_per_group": [int(x) for x in fit.cpu().tolist()],
+                                    "status_all_ok": bool(int(fst.max().item()) == wri.SYS_OK),
+                                    "true_relres": f_true},
+                "speedup_vs_plain_same_rule": t_plain / t_unref3,
+                "speedup_vs_plain_certified": t_plain / t_fused3},
             "speedup_vs_plain_per_system": (t_plain / len(psp)) / (t_tol / nt)}
-        del tsp, psp, fsp
+        del tsp, psp, fsp, usp
         torch.cuda.empty_cache()
 
         if ws == 1:
@@ -624,7 +676,7 @@ def main():
             for g in grads:
                 g.zero_()
             f.zero_()
-            wri.gradient(specs, wri.C64, a, grads=grads, f=f, workspace=work)
+            gradient_of_solve(specs, opts, a, grads, f, work)
             if ws > 1:
                 allreduce_gradient(grads, f)
             for gh, g in zip(g_host, grads):
@@ -647,7 +699,7 @@ def main():
         extras["e2e"] = {"value": ws * nsys * ne / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h}
 
-    launches = step_launches(iters_done, int(opts.poll_every) or K_POLL, True)
+    launches = step_launches(iters_done, int(opts.poll_every) or K_POLL, True, len(groups))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
@@ -661,8 +713,8 @@ def main():
                            "parallelism": f"data parallel x{ws}: one shot record per GPU, gradient all-reduce",
                            "precision": "certified: complex64 CGLS (FP32 stencils and vector updates, FP64 "
                                         "reductions and scalars) inside one FP64 iterative-refinement step (FP64 "
-                                        "wavefield and normal-equation residual); FP64 source estimate and "
-                                        "gradient on the FP64 wavefield",
+                                        "wavefield and normal-equation residual); FP64 source estimate on the FP64 "
+                                        "wavefield and FP64 gradient from the refinement's FP64 residual",
                            "kernel": {"config": int(opts.kernel) - 2 if opts.kernel >= 2 else int(opts.kernel),
                                       "order": int(opts.order),
                                       "chosen_by": "wri_autotune" if args.kernel == 0 and args.order == 0

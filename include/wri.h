@@ -192,6 +192,25 @@ WRI_API int wri_gradient(const wri_group* groups, int ngroups, int dtype, const 
                  double* const* grad, double* f, void* workspace, size_t ws_bytes,
                  wri_stream_t stream);
 
+/* Gradient and objective of Eqs. VarG2 / VarObj2 (the same results as wri_gradient) after a refined
+ * solve, without a stencil pass: wri_solve_batch with max_refine > 0 and u64 on every group ends
+ * with an FP64 residual step, and leaves q = b - S u64 of every system in its workspace.  Its node
+ * part is b1 - Z A u64, and A u - a e = -(b1 - Z A u) (source-free: a = (A u)[src] zeroes the
+ * source row as Z does; known weight: b1 = alpha e), so
+ *   grad[g][k] += -omega^2 sum_i Re( conj(w_k u_ik) q1_ik ),   f[0] += 1/2 ||q1||^2 + 1/2 ||q2||^2
+ * with q2 = lambda (d - P u).  It reads u64 and q once (32 bytes per node and system).
+ *   - Call it after that wri_solve_batch, with the same groups (unchanged arrays) and options and
+ *     the same workspace, on the same stream or after synchronising with it.  The library records
+ *     which problem's residual a workspace holds (a later wri_solve_batch or wri_autotune on the
+ *     workspace drops the record; wri_source_estimate and wri_gradient do not touch that part of
+ *     it) and returns WRI_EINVAL when the record does not match these arguments.
+ *   - grad: host array of ngroups device pointers, each [n_g] double; f: device [1] double; the
+ *     caller zeroes them.  f is summed with FP64 atomics (last-bit order dependence).
+ *   - The source weights, when wanted, come from wri_source_estimate (one stencil per system). */
+WRI_API int wri_gradient_refined(const wri_group* groups, int ngroups, const wri_solve_opts* opts,
+                                 double* const* grad, double* f, const void* workspace, size_t ws_bytes,
+                                 wri_stream_t stream);
+
 /* Allocation-free variant of wri_gradient (the paper has no counterpart: this is an
  * interface for callers that cannot call cudaMalloc, e.g. code whose device memory is
  * owned by another allocator such as a framework's caching pool that has reserved the

@@ -393,6 +393,46 @@ struct Tuned {
 };
 std::vector<Tuned> g_tuned;  // choices of wri_autotune, guarded by g_mu
 
+// Workspaces that hold the FP64 residual b - S u64 of a finished refined solve, with the signature
+// of that solve's problem (wri_gradient_refined reads the residual); guarded by g_mu.
+struct ResidualStamp {
+  const void* ws;
+  std::vector<unsigned long long> sig;
+};
+std::vector<ResidualStamp> g_stamps;
+
+unsigned long long fnv(const void* p, size_t bytes, unsigned long long h = 1469598103934665603ull) {
+  const unsigned char* c = (const unsigned char*)p;
+  for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  return h;
+}
+
+// What the residual left in a workspace depends on: the workspace layout, every group's grid,
+// arrays and geometry, and the precision options.
+std::vector<unsigned long long> residual_signature(const wri_group* groups, int ngroups, const wri_solve_opts* o,
+                                                   size_t total) {
+  std::vector<unsigned long long> sig = {total, (unsigned long long)ngroups, (unsigned long long)o->dtype};
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const wri_group& G = groups[gi];
+    sig.push_back(fnv(&G.grid, sizeof(wri_grid)));
+    const void* ptrs[5] = {G.m, G.d, (const void*)G.alpha, (const void*)G.u, G.u64};
+    for (const void* p : ptrs) sig.push_back((uintptr_t)p);
+    sig.push_back(fnv(&G.lambda, sizeof(double)));
+    sig.push_back((unsigned long long)G.nsys);
+    sig.push_back(fnv(G.src_idx, sizeof(int64_t) * G.nsys));
+    sig.push_back(fnv(G.rec_off, sizeof(int32_t) * (G.nsys + 1)));
+    sig.push_back(fnv(G.rec_idx, sizeof(int32_t) * G.rec_off[G.nsys]));
+  }
+  return sig;
+}
+
+void forget_residual(const void* ws) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_stamps.erase(std::remove_if(g_stamps.begin(), g_stamps.end(),
+                                [&](const ResidualStamp& r) { return r.ws == ws; }),
+                 g_stamps.end());
+}
+
 DevCtx* ctx() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
@@ -1147,6 +1187,7 @@ int wri_solve_batch(const wri_group* groups, int ngroups, const wri_solve_opts* 
   if (rc != WRI_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
+  forget_residual(workspace);
   rc = upload(groups, ngroups, P, ws, st);
   if (rc != WRI_OK) return rc;
   if (opts->plain) {
@@ -1166,6 +1207,10 @@ int wri_solve_batch(const wri_group* groups, int ngroups, const wri_solve_opts* 
       else
         WRI_CK(launch_widen(groups[gi].u, groups[gi].u64, cnt, st));
     }
+  if (P.ir) {  // the workspace now holds b - S u64 in FP64 (the last residual step of every system)
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stamps.push_back({workspace, residual_signature(groups, ngroups, opts, P.total)});
+  }
   return WRI_OK;
 }
 
@@ -1223,6 +1268,36 @@ int wri_gradient(const wri_group* groups, int ngroups, int dtype, const double* 
   return WRI_OK;
 }
 
+int wri_gradient_refined(const wri_group* groups, int ngroups, const wri_solve_opts* opts, double* const* grad,
+                         double* f, const void* workspace, size_t ws_bytes, wri_stream_t stream) {
+  int rc = validate_opts(opts);
+  if (rc != WRI_OK) return rc;
+  rc = validate_groups(groups, ngroups, true);
+  if (rc != WRI_OK) return rc;
+  if (!grad || !f || opts->max_refine < 1 || opts->dtype != WRI_C64) return WRI_EINVAL;
+  for (int gi = 0; gi < ngroups; ++gi)
+    if (!grad[gi] || !groups[gi].u64) return WRI_EINVAL;
+  Plan P;
+  plan_solve(groups, ngroups, opts, P);
+  rc = check_ws(P, workspace, ws_bytes);
+  if (rc != WRI_OK) return rc;
+  {
+    const std::vector<unsigned long long> sig = residual_signature(groups, ngroups, opts, P.total);
+    std::lock_guard<std::mutex> lk(g_mu);
+    bool found = false;
+    for (const auto& r : g_stamps) found = found || (r.ws == workspace && r.sig == sig);
+    if (!found) return WRI_EINVAL;  // the workspace does not hold this problem's residual
+  }
+  char* ws = const_cast<char*>((const char*)workspace);
+  Batch outer = solver_batch(groups, P, ws, false);
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    outer.g[gi].x64 = groups[gi].u64;  // the solve copied its FP64 master there
+    WRI_CK(launch_grad_residual(outer, gi, grad[gi], f, st));
+  }
+  return WRI_OK;
+}
+
 int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int trial_iters, void* workspace,
                  size_t ws_bytes, wri_stream_t stream) {
   int rc = validate_opts(opts);
@@ -1253,6 +1328,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
       }
   }
   cudaStream_t st = (cudaStream_t)stream;
+  forget_residual(workspace);  // the trial solves overwrite the workspace
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   WRI_CK(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {

@@ -32,6 +32,12 @@ cudaError_t launch_loop_ctl(cudaGraphConditionalHandle h, int* counters, int cap
   return cudaGetLastError();
 }
 
+cudaError_t launch_grad_residual(const Batch& b, int gi, double* grad, double* f, cudaStream_t st) {
+  const long long n = b.g[gi].n;
+  k_grad_residual<<<grid_for(n, 256, 8 * 152), 256, 0, st>>>(b, gi, grad, f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ztable(const Batch& b, cudaStream_t st) {
   k_ztable<<<dim3(4, b.ngroups), 128, 0, st>>>(b);
   return cudaGetLastError();

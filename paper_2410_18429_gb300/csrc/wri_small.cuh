@@ -59,6 +59,47 @@ __global__ void k_loop_ctl(cudaGraphConditionalHandle h, int* counters, int cap)
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
+// Gradient and objective of Eqs. VarG2 / VarObj2 from the FP64 residual q = b - S u that a refined
+// solve leaves behind: node part q1 = b1 - Z A u, receiver part q2 = lambda (d - P u).  The PDE
+// residual of the gradient is A u - a e = -q1: in source-free mode a = (A u)[src] zeroes the source
+// row exactly as Z does, and with a known weight b1 = alpha e and Z = I.  So, with no stencil,
+//   grad[node] += -omega^2 sum over the group's systems of Re(conj(w u) q1),
+//   f          += 1/2 ||q1||^2 + 1/2 ||q2||^2.
+// One thread per node of group gi (all its systems); b: the outer view (x64 = u, q64 = q1,
+// r2 = q2 in FP64).
+__global__ void k_grad_residual(const __grid_constant__ Batch b, int gi, double* grad, double* f) {
+  __shared__ double red[8];
+  const GroupDev& G = b.g[gi];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long plane = (long long)G.nx * G.ny;
+  const double2* u = (const double2*)G.x64;
+  const double2* q = (const double2*)G.q64;
+  const double om2 = G.omega * G.omega;
+  double facc = 0.0;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < G.n; node += stride) {
+    const int k = (int)(node / plane);
+    const long long rem = node - (long long)k * plane;
+    const int j = (int)(rem / G.nx);
+    const int i = (int)(rem - (long long)j * G.nx);
+    const double2 w = stretch_at<double, false>(G.ax, double(i)) * stretch_at<double, false>(G.ay, double(j)) *
+                      stretch_at<double, false>(G.az, double(k));
+    double acc = 0.0;
+    for (int sl = 0; sl < G.nsys; ++sl) {
+      const double2 wu = w * u[(long long)sl * G.n + node];
+      const double2 r = q[(long long)sl * G.n + node];
+      acc += wu.x * r.x + wu.y * r.y;
+      facc += 0.5 * abs2(r);
+    }
+    grad[node] += -om2 * acc;
+  }
+  const double2* q2 = (const double2*)b.r2;
+  const int r0 = b.sys[G.sys0].rec_begin, r1 = b.sys[G.sys0 + G.nsys - 1].rec_end;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < r1 - r0; e += stride)
+    facc += 0.5 * abs2(q2[r0 + e]);
+  const double fs = block_sum<256>(facc, red);
+  if (threadIdx.x == 0 && fs != 0.0) atomicAdd(f, fs);
+}
+
 // z-axis coefficient tables of every group (FP32 and FP64, where the batch has them): one thread
 // per (group, plane).
 template <typename R>

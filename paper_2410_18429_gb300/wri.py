@@ -65,6 +65,8 @@ def _load():
     lib.wri_source_estimate.argtypes = [C.POINTER(WriGroup), i32, i32, dp, vp, sz, vp]
     lib.wri_gradient.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp, sz, vp]
     lib.wri_gradient_noalloc.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p), dp, vp]
+    lib.wri_gradient_refined.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), C.POINTER(C.c_void_p), dp,
+                                         vp, sz, vp]
     lib.wri_autotune.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), i32, vp, sz, vp]
     lib.wri_tv.argtypes = [C.POINTER(WriGrid), dp, C.c_double, C.c_double, dp, dp, vp]
     lib.wri_tile_count.argtypes = []
@@ -73,7 +75,8 @@ def _load():
     lib.wri_strerror.restype = C.c_char_p
     lib.wri_version.restype = C.c_char_p
     for f in ("wri_apply_A", "wri_apply_AH", "wri_solve_batch", "wri_source_estimate", "wri_gradient",
-              "wri_gradient_noalloc", "wri_autotune", "wri_tv", "wri_tile_count", "wri_tile_shape"):
+              "wri_gradient_noalloc", "wri_gradient_refined", "wri_autotune", "wri_tv", "wri_tile_count",
+              "wri_tile_shape"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -81,8 +84,8 @@ def _load():
 lib = _load()
 
 EXPORTS = ("wri_apply_A", "wri_apply_AH", "wri_workspace_size", "wri_aux_workspace_size", "wri_solve_batch",
-           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_autotune", "wri_tv", "wri_tile_count",
-           "wri_tile_shape", "wri_strerror", "wri_version")
+           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_gradient_refined", "wri_autotune",
+           "wri_tv", "wri_tile_count", "wri_tile_shape", "wri_strerror", "wri_version")
 
 
 def strerror(code: int) -> str:
@@ -323,6 +326,30 @@ def gradient(groups: Sequence[GroupSpec], dtype: int, alpha, grads=None, f=None,
     gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
     _check(lib.wri_gradient(m.arr, m.n, dtype, _ptr(a), gp, _ptr(f), _ptr(ws), ws.numel(), _stream(stream)),
            "wri_gradient")
+    return grads, f
+
+
+def gradient_refined(groups: Sequence[GroupSpec], opts: WriSolveOpts, workspace, grads=None, f=None, stream=None):
+    """wri_gradient_refined: g and f from the FP64 residual a refined solve left in ``workspace``.
+
+    Call after ``solve(groups, opts, workspace=workspace)`` with max_refine > 0 and u64 on every
+    group, with the same groups, options and workspace.  Returns (gradients, f) like gradient()."""
+    import torch
+    m = _Marshal(groups, int(opts.dtype))
+    dev = groups[0].u.device
+    if grads is None:
+        grads = [torch.zeros(g.nz, g.ny, g.nx, dtype=torch.float64, device=dev) for g in groups]
+    if f is None:
+        f = torch.zeros(1, dtype=torch.float64, device=dev)
+    if len(grads) != len(groups):
+        raise ValueError(f"{len(grads)} gradient buffers for {len(groups)} groups")
+    for i, (g, t) in enumerate(zip(groups, grads)):
+        _device_tensor(t, f"gradient {i}", m.device, torch.float64, g.n)
+    _device_tensor(f, "f", m.device, torch.float64, 1)
+    _device_tensor(workspace, "workspace", m.device)
+    gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
+    _check(lib.wri_gradient_refined(m.arr, m.n, C.byref(opts), gp, _ptr(f), _ptr(workspace), workspace.numel(),
+                                    _stream(stream)), "wri_gradient_refined")
     return grads, f
 
 

@@ -150,6 +150,20 @@ def test_fp64_wavefield_must_be_on_every_group_and_aligned(W):
     assert W.lib.wri_solve_batch(m.arr, 2, C.byref(o), 0x100, 0x200, 0x300, 0x1000, 1 << 40, None) == W.EINVAL
 
 
+def test_gradient_refined_needs_a_refined_solve_of_the_same_problem(W):
+    """wri_gradient_refined: no refinement in the options, no FP64 wavefield, or a workspace that holds
+    no residual of this problem are argument errors, caught before any device work."""
+    g = _spec(W, u64=_FakeTensor(0x20000))
+    m = W._Marshal([g])
+    gp = (C.c_void_p * 1)(0x4000)
+    ref = W.make_opts(max_refine=1)
+    assert W.lib.wri_gradient_refined(m.arr, 1, C.byref(ref), gp, 0x6000, 0x100000, 1 << 40, None) == W.EINVAL
+    assert W.lib.wri_gradient_refined(m.arr, 1, C.byref(W.make_opts()), gp, 0x6000, 0x100000, 1 << 40,
+                                      None) == W.EINVAL
+    m2 = W._Marshal([_spec(W)])
+    assert W.lib.wri_gradient_refined(m2.arr, 1, C.byref(ref), gp, 0x6000, 0x100000, 1 << 40, None) == W.EINVAL
+
+
 def test_tv_rejects_invalid_arguments(W):
     g = W.WriGrid(20, 18, 16, 3, 10.0, 60.0, 1e-3, 2000.0)
     assert W.lib.wri_tv(C.byref(g), 0x1000, 0.0, 1.0, 0x2000, None, None) == W.EINVAL      # beta = 0

@@ -373,6 +373,47 @@ def test_pipeline_gradient_matches_oracle(W):
     assert abs(f.item() - f_ex) <= 1e-4 * abs(f_ex)
 
 
+@pytest.mark.parametrize("source_free", [True, False])
+def test_gradient_from_refined_residual_equals_stencil_gradient(W, source_free):
+    """wri_gradient_refined reads the FP64 residual a refined solve leaves in its workspace: the same f
+    and g as wri_gradient's FP64 stencil pass on the FP64 wavefield (to rounding), with two frequency
+    groups in one call.  The library's record of which problem's residual a workspace holds guards the
+    call."""
+    G1 = case(nphys=(17, 12, 9), npml=3, nsys=3, freq=14.0)
+    G2 = case(nphys=(12, 10, 8), npml=3, nsys=2, seed=8, freq=9.0)
+    specs = [_spec(W, G, 0, source_free) for G in (G1, G2)]
+    for sp in specs:
+        sp.u64 = torch.zeros(sp.nsys, sp.n, dtype=torch.complex128, device="cuda")
+    opts = W.make_opts(tol=1e-3, max_iter=200000, dtype=0, max_refine=12, refine_tol=1e-9, inner_tol=1e-3)
+    work = torch.empty(W.workspace_size(specs, opts), dtype=torch.uint8, device="cuda")
+    it, rr, st = W.solve(specs, opts, workspace=work)
+    assert st.cpu().tolist() == [W.SYS_OK] * 5
+    g_res, f_res = W.gradient_refined(specs, opts, work)
+    a = W.source_estimate(specs, 0) if source_free else torch.view_as_complex(
+        torch.cat([sp.alpha for sp in specs]).contiguous())
+    g_st, f_st = W.gradient(specs, 0, a)
+    for x, y in zip(g_res, g_st):
+        assert rel(x.cpu().numpy(), y.cpu().numpy()) < 1e-9
+    assert abs(f_res.item() - f_st.item()) <= 1e-10 * abs(f_st.item())
+    # the residual of a fixed-budget refined solve (the benchmark's step) is also the right one
+    fixed = W.make_opts(tol=0.0, max_iter=40, dtype=0, max_refine=1, refine_tol=0.0, inner_tol=1e-300)
+    W.solve(specs, fixed, workspace=work)
+    g_res, f_res = W.gradient_refined(specs, fixed, work)
+    g_st, f_st = W.gradient(specs, 0, W.source_estimate(specs, 0) if source_free else a)
+    for x, y in zip(g_res, g_st):
+        assert rel(x.cpu().numpy(), y.cpu().numpy()) < 1e-9
+    # an unrefined solve on the workspace drops the record, and so does a refined solve of other
+    # groups: the call is refused rather than reading a residual of another problem
+    W.solve(specs, W.make_opts(tol=0.0, max_iter=5, dtype=0), workspace=work)
+    with pytest.raises(W.WriError) as e:
+        W.gradient_refined(specs, fixed, work)
+    assert e.value.code == W.EINVAL
+    W.solve(specs[:1], fixed, workspace=work)
+    with pytest.raises(W.WriError) as e:
+        W.gradient_refined(specs, fixed, work)
+    assert e.value.code == W.EINVAL
+
+
 # ------------------------------------------------------------------ batching (a4)
 def test_batched_equals_unbatched_and_multi_group(W):
     G1 = case(nphys=(25, 12, 10), npml=4, nsys=3, seed=5)
