@@ -96,7 +96,9 @@ typedef struct {
   const int32_t* rec_idx;   /* host [rec_off[nsys]] receiver nodes; distinct within a system */
   const void* d;            /* device [rec_off[nsys]] observed data (complex, dtype) */
   const double* alpha;      /* device [2*nsys] known weights (complex128) or NULL = source-free */
-  double lambda;            /* data weight, > 0 */
+  double lambda;            /* data weight, > 0; 0 allowed with a known right-hand side (alpha or q):
+                               then the solve is the PDE least-squares problem min ||A u - b1||
+                               (the forward and adjoint solves of reduced FWI, Eqs. PDEsolve / FWI2) */
   void* u;                  /* device [nsys][n] complex (dtype): in = x0 if warm_start, out = u */
   void* u64;                /* WRI_C64 only, optional: device [nsys][n] complex128 (16-byte aligned)
                                or NULL.  wri_solve_batch also writes the solution here, in FP64
@@ -105,6 +107,9 @@ typedef struct {
                                FP64 stencils: the gradient needs the PDE residual A u - a e, which
                                rounding u to complex64 would swamp.  In one call either every
                                group sets it or none does.  Ignored for WRI_C128. */
+  const void* q;            /* device [nsys][n] complex (dtype) or NULL: a general PDE right-hand side,
+                               b1 = q in place of alpha e (Z = I); alpha must then be NULL.  The
+                               adjoint solve of reduced FWI uses it (see wri_fwi_adjoint_source). */
 } wri_group;
 
 typedef struct {
@@ -210,6 +215,34 @@ WRI_API int wri_gradient(const wri_group* groups, int ngroups, int dtype, const 
 WRI_API int wri_gradient_refined(const wri_group* groups, int ngroups, const wri_solve_opts* opts,
                                  double* const* grad, double* f, const void* workspace, size_t ws_bytes,
                                  wri_stream_t stream);
+
+/* Reduced FWI, the paper's comparison method (Eqs. FWI, PDEsolve and FWI2), on libwri's solves:
+ *   1. forward solves A G_i = e_i: wri_solve_batch with alpha = 1 and lambda = 0 (u = G);
+ *   2. wri_fwi_adjoint_source: the weights a_i (given, or source-free the minimiser of
+ *      ||a P G_i - d_i||: a_i = (P G_i)^H d_i / ||P G_i||^2), the data residuals
+ *      r_i = a_i P G_i - d_i, f += 1/2 sum ||r_i||^2 (Eq. FWI2), and the adjoint right-hand sides
+ *      conj(P^T r_i);
+ *   3. adjoint solves A w_i = conj(P^T r_i): wri_solve_batch with q set and lambda = 0.  A is
+ *      complex symmetric, so v_i = conj(w_i) solves A^H v_i = P^T r_i;
+ *   4. wri_fwi_gradient: grad[k] += -omega^2 sum_i Re(w_k a_i G_ik conj(v_ik))
+ *      = -omega^2 sum_i Re(w_k a_i G_ik w_ik)  (the adjoint-state gradient; the weight's own
+ *      derivative vanishes at its optimum).
+ * groups: the forward solves' groups (grid, m, geometry, d; u = G).
+ *   alpha_in:  device [2 * sum nsys] complex128 known weights, or NULL (source-free)
+ *   alpha_out: device [2 * sum nsys] complex128, the weights used
+ *   q_adj:     host array of ngroups device pointers, each [nsys][n] complex (dtype); written only
+ *              at the receiver nodes, so the caller zeroes them first
+ *   f:         device [1] double, accumulated (FP64 atomics)
+ *   workspace: >= wri_aux_workspace_size(groups, ngroups) */
+WRI_API int wri_fwi_adjoint_source(const wri_group* groups, int ngroups, int dtype, const double* alpha_in,
+                                   double* alpha_out, void* const* q_adj, double* f, void* workspace,
+                                   size_t ws_bytes, wri_stream_t stream);
+/*   w: host array of ngroups device pointers, each [nsys][n] complex (dtype), the adjoint solves'
+ *      wavefields; alpha: the weights of wri_fwi_adjoint_source; grad: host array of ngroups device
+ *      pointers, each [n] double, accumulated (the caller zeroes them).  Systems of a group are
+ *      summed in a fixed order per node. */
+WRI_API int wri_fwi_gradient(const wri_group* groups, int ngroups, int dtype, const double* alpha,
+                             void* const* w, double* const* grad, wri_stream_t stream);
 
 /* Allocation-free variant of wri_gradient (the paper has no counterpart: this is an
  * interface for callers that cannot call cudaMalloc, e.g. code whose device memory is

@@ -139,7 +139,9 @@ int validate_groups(const wri_group* groups, int ngroups, bool need_data) {
     const wri_group& G = groups[gi];
     if (!grid_valid(&G.grid)) return WRI_EINVAL;
     if (!G.m || !G.u || G.nsys < 1 || !G.src_idx || !G.rec_off || !G.rec_idx) return WRI_EINVAL;
-    if (!(G.lambda > 0) || !std::isfinite(G.lambda)) return WRI_EINVAL;
+    if (!(G.lambda >= 0) || !std::isfinite(G.lambda)) return WRI_EINVAL;
+    if (G.alpha && G.q) return WRI_EINVAL;                   // one right-hand side
+    if (G.lambda == 0 && !G.alpha && !G.q) return WRI_EINVAL;  // source-free needs the data term
     const long long n = grid_n(G.grid);
     if (G.rec_off[0] != 0) return WRI_EINVAL;
     for (int s = 0; s < G.nsys; ++s) {
@@ -415,7 +417,7 @@ std::vector<unsigned long long> residual_signature(const wri_group* groups, int 
   for (int gi = 0; gi < ngroups; ++gi) {
     const wri_group& G = groups[gi];
     sig.push_back(fnv(&G.grid, sizeof(wri_grid)));
-    const void* ptrs[5] = {G.m, G.d, (const void*)G.alpha, (const void*)G.u, G.u64};
+    const void* ptrs[6] = {G.m, G.d, (const void*)G.alpha, (const void*)G.u, G.u64, G.q};
     for (const void* p : ptrs) sig.push_back((uintptr_t)p);
     sig.push_back(fnv(&G.lambda, sizeof(double)));
     sig.push_back((unsigned long long)G.nsys);
@@ -475,11 +477,13 @@ Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_
     GroupDev G = P.g[gi];
     const wri_group& U = groups[gi];
     G.lambda = U.lambda;
-    G.masked = U.alpha ? 0 : 1;
+    G.masked = (U.alpha || U.q) ? 0 : 1;
     G.m = U.m;
     G.m_double = P.dtype == WRI_C128 ? 1 : 0;
     G.d = U.d;
     G.alpha = U.alpha;
+    G.q = U.q;
+    G.q_double = P.dtype == WRI_C128 ? 1 : 0;
     G.r1[0] = ws + P.v_r1[gi][0];
     G.r1[1] = ws + P.v_r1[gi][1];
     G.p[0] = ws + P.v_p[gi][0];
@@ -893,7 +897,7 @@ int solve_plain(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
     const wri_group& U = groups[gi];
     GroupDev G1 = P.g[gi];
     G1.lambda = U.lambda;
-    G1.masked = U.alpha ? 0 : 1;
+    G1.masked = (U.alpha || U.q) ? 0 : 1;
     G1.m = U.m;
     G1.m_double = P.dtype == WRI_C128 ? 1 : 0;
     decompose(U.grid, P.by, o->zsplit > 0 ? o->zsplit : auto_zsplit((long long)G1.tiles_x * G1.tiles_y, U.grid.nz),
@@ -946,6 +950,8 @@ int solve_plain(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
         ai = pinned_d[1];
       }
       WRI_CK(plain_fill(rb, r1, x, n, U.alpha ? sd.src : -1, ar, ai, st));
+      if (U.q)  // general right-hand side: r1 = b1 = q
+        WRI_CK(cudaMemcpyAsync(r1, (const char*)U.q + (size_t)l * n * cb, (size_t)n * cb, cudaMemcpyDeviceToDevice, st));
       WRI_CK(plain_setr2(rb, r2, dd, nr, U.lambda, st));
       WRI_CK(apply(r1, s, true));
       WRI_CK(plain_scatter(rb, s, rc, r2, nr, U.lambda, st));
@@ -958,7 +964,7 @@ int solve_plain(const wri_group* groups, int ngroups, const wri_solve_opts* o, c
         WRI_CK(cudaMemcpyAsync(p, s, (size_t)n * cb, cudaMemcpyDeviceToDevice, st));
         for (;;) {
           WRI_CK(apply(p, t1, false));
-          WRI_CK(plain_gather_mask(rb, t2, p, rc, nr, U.lambda, t1, sd.src, U.alpha ? 0 : 1, st));
+          WRI_CK(plain_gather_mask(rb, t2, p, rc, nr, U.lambda, t1, sd.src, (U.alpha || U.q) ? 0 : 1, st));
           double delta = 0.0;
           if (dot2(t1, n, t2, nr, delta) != WRI_OK) return WRI_ECUDA;
           if (!(delta > 0) || !std::isfinite(delta)) {
@@ -1057,8 +1063,9 @@ Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, i
   b.ngroups = ngroups;
   b.bx = WRI_TX;
   b.by = 8;
-  b.sys = (SysDev*)(ws + P.off_sys);
-  b.rec_idx = (const int*)(ws + P.off_rec);
+  // ws == nullptr: a geometry-only batch (no device copy of the systems, no tables)
+  b.sys = ws ? (SysDev*)(ws + P.off_sys) : nullptr;
+  b.rec_idx = ws ? (const int*)(ws + P.off_rec) : nullptr;
   int sys0 = 0;
   long long item = 0;
   for (int gi = 0; gi < ngroups; ++gi) {
@@ -1067,13 +1074,15 @@ Batch aux_batch(const wri_group* groups, int ngroups, const Plan& P, char* ws, i
     G.lambda = groups[gi].lambda;
     G.nsys = groups[gi].nsys;
     G.sys0 = sys0;
-    G.masked = groups[gi].alpha ? 0 : 1;
+    G.masked = (groups[gi].alpha || groups[gi].q) ? 0 : 1;
+    G.q = groups[gi].q;
+    G.q_double = dtype == WRI_C128 ? 1 : 0;
     G.m = groups[gi].m;
     G.m_double = dtype == WRI_C128 ? 1 : 0;
     G.d = groups[gi].d;
     G.x = wide ? groups[gi].u64 : groups[gi].u;
-    G.ztab = (const float2*)(ws + P.off_ztab[gi]);
-    G.ztab64 = (const double2*)(ws + P.off_ztab64[gi]);
+    G.ztab = ws ? (const float2*)(ws + P.off_ztab[gi]) : nullptr;
+    G.ztab64 = ws ? (const double2*)(ws + P.off_ztab64[gi]) : nullptr;
     // gradient decomposition: one work item per tile, systems looped inside
     G.tiles_x = (G.nx + WRI_TX - 1) / WRI_TX;
     G.tiles_y = (G.ny + 7) / 8;
@@ -1295,6 +1304,45 @@ int wri_gradient_refined(const wri_group* groups, int ngroups, const wri_solve_o
     outer.g[gi].x64 = groups[gi].u64;  // the solve copied its FP64 master there
     WRI_CK(launch_grad_residual(outer, gi, grad[gi], f, st));
   }
+  return WRI_OK;
+}
+
+int wri_fwi_adjoint_source(const wri_group* groups, int ngroups, int dtype, const double* alpha_in, double* alpha_out,
+                           void* const* q_adj, double* f, void* workspace, size_t ws_bytes, wri_stream_t stream) {
+  if (dtype != WRI_C64 && dtype != WRI_C128) return WRI_EINVAL;
+  int rc = validate_groups(groups, ngroups, true);
+  if (rc != WRI_OK) return rc;
+  if (!alpha_out || !q_adj || !f) return WRI_EINVAL;
+  for (int gi = 0; gi < ngroups; ++gi)
+    if (!q_adj[gi]) return WRI_EINVAL;
+  Plan P;
+  plan_aux(groups, ngroups, P);
+  rc = check_ws(P, workspace, ws_bytes);
+  if (rc != WRI_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  rc = upload(groups, ngroups, P, ws, st);
+  if (rc != WRI_OK) return rc;
+  const Batch b = aux_batch(groups, ngroups, P, ws, dtype);
+  WRI_CK(launch_fwi_adjoint_source(dtype == WRI_C128 ? 8 : 4, b, P.nsys_total, alpha_in, alpha_out, q_adj, f, st));
+  return WRI_OK;
+}
+
+int wri_fwi_gradient(const wri_group* groups, int ngroups, int dtype, const double* alpha, void* const* w,
+                     double* const* grad, wri_stream_t stream) {
+  if (dtype != WRI_C64 && dtype != WRI_C128) return WRI_EINVAL;
+  int rc = validate_groups(groups, ngroups, false);
+  if (rc != WRI_OK) return rc;
+  if (!alpha || !w || !grad) return WRI_EINVAL;
+  for (int gi = 0; gi < ngroups; ++gi)
+    if (!w[gi] || !grad[gi]) return WRI_EINVAL;
+  Plan P;
+  plan_aux(groups, ngroups, P);
+  // geometry only: no workspace is read (the batch's workspace views stay unset)
+  const Batch b = aux_batch(groups, ngroups, P, nullptr, dtype);
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int gi = 0; gi < ngroups; ++gi)
+    WRI_CK(launch_fwi_gradient(dtype == WRI_C128 ? 8 : 4, b, gi, alpha, w[gi], grad[gi], st));
   return WRI_OK;
 }
 

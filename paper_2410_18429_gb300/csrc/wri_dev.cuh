@@ -134,12 +134,14 @@ struct GroupDev {
   int nsys, sys0;          // systems of the group and global index of the first
   int tiles_x, tiles_y, zsplit, zc, ntiles;
   long long item0, nitems;  // work items (tile x system) of the group in the batched launch
-  int masked;               // 1 = source-free (Z applied), 0 = known weight
+  int masked;               // 1 = source-free (Z applied), 0 = known weight or general right-hand side
   long long n;              // nodes
   const void* m;            // [n] real, float or double (m_double)
   int m_double;             // 1 if m is double (complex128 problems), 0 if float
   const void* d;            // [nnz] complex observed data
   const double* alpha;      // [2*nsys] known weights or null
+  const void* q;            // [nsys][n] general PDE right-hand side b1 (complex, q_double), or null
+  int q_double;             // 1 if q is double2 (complex128 problems), 0 if float2
   void* x;                  // [nsys][n] iterate (dtype of the stencil)
   void* r1[2];              // [nsys][n] data-space residual, ping-pong
   void* p[2];               // [nsys][n] search direction, ping-pong

@@ -32,6 +32,11 @@ cudaError_t launch_ir_update(const Batch& b, cudaStream_t st);
 cudaError_t launch_ir_final(const Batch& b, void* const* u, cudaStream_t st);
 cudaError_t launch_source_estimate(int rbytes, const Batch& b, int nsys_total, double* alpha_out, cudaStream_t st);
 cudaError_t launch_data_term(int rbytes, int dbytes, const Batch& b, int nsys_total, cudaStream_t st);
+// reduced FWI: weights, residuals, objective and adjoint right-hand sides; gradient of group gi
+cudaError_t launch_fwi_adjoint_source(int rbytes, const Batch& b, int nsys_total, const double* alpha_in,
+                                      double* alpha_out, void* const* q_adj, double* f, cudaStream_t st);
+cudaError_t launch_fwi_gradient(int rbytes, const Batch& b, int gi, const double* alpha, const void* w, double* grad,
+                                cudaStream_t st);
 // gradient and objective from a refined solve's FP64 residual (b: outer view of that solve)
 cudaError_t launch_grad_residual(const Batch& b, int gi, double* grad, double* f, cudaStream_t st);
 cudaError_t launch_widen(const void* u, void* u64, long long count, cudaStream_t st);

@@ -102,6 +102,14 @@ __device__ __forceinline__ ZCoef<R> z_coef(const GroupDev& G, int k) {
   return c;
 }
 
+// General right-hand side b1 = q of system sl at a node, in the precision of the kernel.
+template <typename R>
+__device__ __forceinline__ cx<R> q_at(const GroupDev& G, int sl, long long node) {
+  const long long e = (long long)sl * G.n + node;
+  if (G.q_double) return to_c(((const double2*)G.q)[e], R(0));
+  return to_c(((const float2*)G.q)[e], R(0));
+}
+
 // z-axis coefficients of plane k from the per-call table (no FP64 division per node-plane on the
 // narrow FP64 pipe), or computed when the call built no table.
 __device__ __forceinline__ const float2* ztab_of(const GroupDev& G, float) { return G.ztab; }

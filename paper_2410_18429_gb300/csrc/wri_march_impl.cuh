@@ -280,10 +280,15 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
         const uint32_t rcb = ((MODE == M_P2 || (MODE == M_SH && !G.rmap)) && own)
                                  ? (rec_col_bits(G, sl, j, x0) >> tx) & 1u : 0u;
 
-        // field F = Fa + coef * Fb, or the point field b1 = alpha e (cold start)
+        // field F = Fa + coef * Fb, or the right-hand side b1 (cold start): the point field alpha e,
+        // 0 (source-free) or the general right-hand side q
         const bool point = (MODE == M_SH) && (b.flavor == SH_INIT || b.flavor == SH_REF);
         C pval = czero<R>();
-        if (point && !G.masked) pval = mkc(R(G.alpha[2 * sl]), R(G.alpha[2 * sl + 1]));
+        if (point && G.alpha) pval = mkc(R(G.alpha[2 * sl]), R(G.alpha[2 * sl + 1]));
+        auto b1_at = [&](long long node) -> C {
+          if (G.q) return q_at<R>(G, sl, node);
+          return (node == src) ? pval : czero<R>();
+        };
         const C* Fa = nullptr;
         const C* Fb = nullptr;
         C* Fst = nullptr;
@@ -309,12 +314,11 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
           Fst = (C*)G.r1[cur ^ 1] + off;
         }
         C a_src = czero<R>();
-        if (MODE == M_RES && !G.masked) a_src = mkc(R(G.alpha[2 * sl]), R(G.alpha[2 * sl + 1]));
-        if (MODE == M_GRAD) a_src = mkc(R(G.alpha[2 * sl]), R(G.alpha[2 * sl + 1]));
+        if ((MODE == M_RES || MODE == M_GRAD) && G.alpha) a_src = mkc(R(G.alpha[2 * sl]), R(G.alpha[2 * sl + 1]));
 
         // F at any node (no side effects)
         auto fieldF = [&](long long node) -> C {
-          if (point) return (node == src) ? pval : czero<R>();
+          if (point) return b1_at(node);
           C v = ldg_c<R>(Fa + node);
           if (Fb) v = v + coef * ldg_c<R>(Fb + node);
           return v;
@@ -325,7 +329,7 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
           const long long node = kk * plane + col;
           const bool mine = (kk >= z0) && (kk < z1);
           if (point) {
-            const C v = (node == src) ? pval : czero<R>();
+            const C v = b1_at(node);
             if (mine) {
               Fst[node] = v;
               if (X) X[node] = czero<R>();
@@ -410,7 +414,8 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
               }
             } else if (MODE == M_RES) {
               C r = czero<R>() - AF;
-              if (node == src) r = G.masked ? czero<R>() : a_src - AF;
+              if (G.q) r = q_at<R>(G, sl, node) - AF;
+              else if (node == src) r = G.masked ? czero<R>() : a_src - AF;
               ((C*)G.r1[0])[gnode] = r;
             } else if (MODE == M_P1) {
               const C t = (G.masked && node == src) ? czero<R>() : AF;
@@ -428,7 +433,8 @@ __global__ void __launch_bounds__(WRI_TX * BY) k_march(const __grid_constant__ B
               }
             } else if (MODE == M_GRAD) {
               C r = AF;
-              if (node == src) r = r - a_src;
+              if (G.q) r = r - q_at<R>(G, sl, node);
+              else if (node == src) r = r - a_src;
               if (fast) {
                 gacc[k - z0][ty][tx] += (double)(om2 * (u.x * r.x + u.y * r.y));
               } else {

@@ -38,6 +38,24 @@ cudaError_t launch_grad_residual(const Batch& b, int gi, double* grad, double* f
   return cudaGetLastError();
 }
 
+cudaError_t launch_fwi_adjoint_source(int rbytes, const Batch& b, int nsys_total, const double* alpha_in,
+                                      double* alpha_out, void* const* q_adj, double* f, cudaStream_t st) {
+  if (nsys_total <= 0) return cudaSuccess;
+  FwiPtrs Q;
+  for (int g = 0; g < WRI_MAXG; ++g) Q.p[g] = g < b.ngroups ? q_adj[g] : nullptr;
+  if (rbytes == 8) k_fwi_adjoint_source<double><<<nsys_total, 128, 0, st>>>(b, nsys_total, alpha_in, alpha_out, Q, f);
+  else k_fwi_adjoint_source<float><<<nsys_total, 128, 0, st>>>(b, nsys_total, alpha_in, alpha_out, Q, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwi_gradient(int rbytes, const Batch& b, int gi, const double* alpha, const void* w, double* grad,
+                                cudaStream_t st) {
+  const int grid = grid_for(b.g[gi].n, 256, 8 * 152);
+  if (rbytes == 8) k_fwi_gradient<double><<<grid, 256, 0, st>>>(b, gi, alpha, w, grad);
+  else k_fwi_gradient<float><<<grid, 256, 0, st>>>(b, gi, alpha, w, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ztable(const Batch& b, cudaStream_t st) {
   k_ztable<<<dim3(4, b.ngroups), 128, 0, st>>>(b);
   return cudaGetLastError();

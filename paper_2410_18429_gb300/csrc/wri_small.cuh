@@ -100,6 +100,96 @@ __global__ void k_grad_residual(const __grid_constant__ Batch b, int gi, double*
   if (threadIdx.x == 0 && fs != 0.0) atomicAdd(f, fs);
 }
 
+// ------------------------------------------------------------------ reduced FWI (Eqs. PDEsolve, FWI2)
+struct FwiPtrs {
+  void* p[WRI_MAXG];  // one device array per group, [nsys][n] complex
+};
+
+// Weights, data residuals, objective and adjoint right-hand sides of reduced FWI: one block of 128
+// threads per system.  u = G = A^{-1} e (the forward solve with weight 1) in b.g[].x; the weight a
+// is given or, source-free, the minimiser of ||a P G - d||: a = (P G)^H d / ||P G||^2; then
+// r = a P G - d, f += 1/2 ||r||^2 and q_adj = conj(P^T r) (A complex symmetric: the solve of
+// A w = q_adj gives the adjoint wavefield v = conj(w) of A^H v = P^T r).
+template <typename R>
+__global__ void k_fwi_adjoint_source(const __grid_constant__ Batch b, int nsys_total, const double* alpha_in,
+                                     double* alpha_out, FwiPtrs Q, double* f) {
+  __shared__ double red[4];
+  const int s = blockIdx.x;
+  if (s >= nsys_total) return;
+  const SysDev& sd = b.sys[s];
+  const GroupDev& G = b.g[sd.group];
+  const cx<R>* u = (const cx<R>*)G.x + (long long)sd.local * G.n;
+  const cx<R>* d = (const cx<R>*)G.d;
+  const int base = b.sys[G.sys0].rec_begin;  // the group's data starts at its first system
+  double a_re, a_im;
+  if (alpha_in) {
+    a_re = alpha_in[2 * s];
+    a_im = alpha_in[2 * s + 1];
+  } else {
+    double nr = 0.0, ni = 0.0, den = 0.0;  // (P G)^H d and ||P G||^2
+    for (int k = sd.rec_begin + threadIdx.x; k < sd.rec_end; k += blockDim.x) {
+      const double2 g = to_c(u[b.rec_idx[k]], 0.0), dv = to_c(d[k - base], 0.0);
+      nr += g.x * dv.x + g.y * dv.y;
+      ni += g.x * dv.y - g.y * dv.x;
+      den += g.x * g.x + g.y * g.y;
+    }
+    nr = block_sum<128>(nr, red);
+    ni = block_sum<128>(ni, red);
+    den = block_sum<128>(den, red);
+    __shared__ double sa[2];
+    if (threadIdx.x == 0) {
+      sa[0] = den > 0.0 ? nr / den : 0.0;
+      sa[1] = den > 0.0 ? ni / den : 0.0;
+    }
+    __syncthreads();
+    a_re = sa[0];
+    a_im = sa[1];
+  }
+  if (threadIdx.x == 0) {
+    alpha_out[2 * s] = a_re;
+    alpha_out[2 * s + 1] = a_im;
+  }
+  cx<R>* q = (cx<R>*)Q.p[sd.group] + (long long)sd.local * G.n;
+  double fr = 0.0;
+  for (int k = sd.rec_begin + threadIdx.x; k < sd.rec_end; k += blockDim.x) {
+    const int node = b.rec_idx[k];
+    const double2 g = to_c(u[node], 0.0), dv = to_c(d[k - base], 0.0);
+    const double2 r = make_double2(a_re * g.x - a_im * g.y - dv.x, a_re * g.y + a_im * g.x - dv.y);
+    fr += 0.5 * (r.x * r.x + r.y * r.y);
+    q[node] = to_c(make_double2(r.x, -r.y), R(0));
+  }
+  fr = block_sum<128>(fr, red);
+  if (threadIdx.x == 0 && fr != 0.0) atomicAdd(f, fr);
+}
+
+// Gradient of reduced FWI for group gi: one thread per node, the group's systems summed in order:
+// grad += -omega^2 sum_i Re(w a_i G_i conj(v_i)) with conj(v_i) = w_i, the adjoint solve's wavefield.
+template <typename R>
+__global__ void k_fwi_gradient(const __grid_constant__ Batch b, int gi, const double* alpha, const void* wadj,
+                               double* grad) {
+  const GroupDev& G = b.g[gi];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long plane = (long long)G.nx * G.ny;
+  const cx<R>* u = (const cx<R>*)G.x;
+  const cx<R>* wv = (const cx<R>*)wadj;
+  const double om2 = G.omega * G.omega;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < G.n; node += stride) {
+    const int k = (int)(node / plane);
+    const long long rem = node - (long long)k * plane;
+    const int j = (int)(rem / G.nx);
+    const int i = (int)(rem - (long long)j * G.nx);
+    const double2 w = stretch_at<double, false>(G.ax, double(i)) * stretch_at<double, false>(G.ay, double(j)) *
+                      stretch_at<double, false>(G.az, double(k));
+    double acc = 0.0;
+    for (int sl = 0; sl < G.nsys; ++sl) {
+      const double2 a = make_double2(alpha[2 * (G.sys0 + sl)], alpha[2 * (G.sys0 + sl) + 1]);
+      const double2 t = (w * a) * to_c(u[(long long)sl * G.n + node], 0.0) * to_c(wv[(long long)sl * G.n + node], 0.0);
+      acc += t.x;
+    }
+    grad[node] += -om2 * acc;
+  }
+}
+
 // z-axis coefficient tables of every group (FP32 and FP64, where the batch has them): one thread
 // per (group, plane).
 template <typename R>

@@ -32,7 +32,7 @@ class WriGrid(C.Structure):
 class WriGroup(C.Structure):
     _fields_ = [("grid", WriGrid), ("m", C.c_void_p), ("nsys", C.c_int32), ("src_idx", C.c_void_p),
                 ("rec_off", C.c_void_p), ("rec_idx", C.c_void_p), ("d", C.c_void_p), ("alpha", C.c_void_p),
-                ("lam", C.c_double), ("u", C.c_void_p), ("u64", C.c_void_p)]
+                ("lam", C.c_double), ("u", C.c_void_p), ("u64", C.c_void_p), ("q", C.c_void_p)]
 
 
 class WriSolveOpts(C.Structure):
@@ -68,6 +68,10 @@ def _load():
     lib.wri_gradient_refined.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), C.POINTER(C.c_void_p), dp,
                                          vp, sz, vp]
     lib.wri_autotune.argtypes = [C.POINTER(WriGroup), i32, C.POINTER(WriSolveOpts), i32, vp, sz, vp]
+    lib.wri_fwi_adjoint_source.argtypes = [C.POINTER(WriGroup), i32, i32, dp, dp, C.POINTER(C.c_void_p), dp, vp, sz,
+                                           vp]
+    lib.wri_fwi_gradient.argtypes = [C.POINTER(WriGroup), i32, i32, dp, C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_void_p), vp]
     lib.wri_tv.argtypes = [C.POINTER(WriGrid), dp, C.c_double, C.c_double, dp, dp, vp]
     lib.wri_tile_count.argtypes = []
     lib.wri_tile_shape.argtypes = [i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -75,8 +79,8 @@ def _load():
     lib.wri_strerror.restype = C.c_char_p
     lib.wri_version.restype = C.c_char_p
     for f in ("wri_apply_A", "wri_apply_AH", "wri_solve_batch", "wri_source_estimate", "wri_gradient",
-              "wri_gradient_noalloc", "wri_gradient_refined", "wri_autotune", "wri_tv", "wri_tile_count",
-              "wri_tile_shape"):
+              "wri_gradient_noalloc", "wri_gradient_refined", "wri_fwi_adjoint_source", "wri_fwi_gradient",
+              "wri_autotune", "wri_tv", "wri_tile_count", "wri_tile_shape"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -84,8 +88,9 @@ def _load():
 lib = _load()
 
 EXPORTS = ("wri_apply_A", "wri_apply_AH", "wri_workspace_size", "wri_aux_workspace_size", "wri_solve_batch",
-           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_gradient_refined", "wri_autotune",
-           "wri_tv", "wri_tile_count", "wri_tile_shape", "wri_strerror", "wri_version")
+           "wri_source_estimate", "wri_gradient", "wri_gradient_noalloc", "wri_gradient_refined",
+           "wri_fwi_adjoint_source", "wri_fwi_gradient", "wri_autotune", "wri_tv", "wri_tile_count",
+           "wri_tile_shape", "wri_strerror", "wri_version")
 
 
 def strerror(code: int) -> str:
@@ -121,6 +126,8 @@ class GroupSpec:
     u: complex CUDA tensor [nsys, n] (initial guess with warm_start, result on return).
     u64: optional complex128 CUDA tensor [nsys, n] for complex64 problems: the solve also writes
     the FP64 solution there, and the source estimate and gradient then read it (FP64 stencils).
+    q: optional complex CUDA tensor [nsys, n] (dtype of u): a general PDE right-hand side b1 = q in
+    place of alpha e (alpha must then be None); lam may be 0 when alpha or q is given.
     """
 
     nx: int
@@ -140,6 +147,7 @@ class GroupSpec:
     alpha: object = None
     pml_R: float = 1e-3
     u64: object = None
+    q: object = None
 
     @property
     def n(self) -> int:
@@ -206,11 +214,12 @@ class _Marshal:
             dev = _device_tensor(g.u, f"group {i}: u", dev, cplx, nsys * n)
             dev = _device_tensor(g.alpha, f"group {i}: alpha", dev, torch.float64, 2 * nsys)
             dev = _device_tensor(g.u64, f"group {i}: u64", dev, torch.complex128, nsys * n)
+            dev = _device_tensor(g.q, f"group {i}: q", dev, cplx, nsys * n)
             if len(rec) == 0:
                 rec = np.zeros(1, dtype=np.int32)
             self.keep += [src, off, rec]
             arr[i] = WriGroup(g.grid(), _ptr(g.m), len(src), src.ctypes.data, off.ctypes.data, rec.ctypes.data,
-                              _ptr(g.d), _ptr(g.alpha), float(g.lam), _ptr(g.u), _ptr(g.u64))
+                              _ptr(g.d), _ptr(g.alpha), float(g.lam), _ptr(g.u), _ptr(g.u64), _ptr(g.q))
         self.arr = arr
         self.n = len(groups)
         self.device = dev
@@ -351,6 +360,56 @@ def gradient_refined(groups: Sequence[GroupSpec], opts: WriSolveOpts, workspace,
     _check(lib.wri_gradient_refined(m.arr, m.n, C.byref(opts), gp, _ptr(f), _ptr(workspace), workspace.numel(),
                                     _stream(stream)), "wri_gradient_refined")
     return grads, f
+
+
+def fwi_adjoint_source(groups: Sequence[GroupSpec], dtype: int, q_adj, alpha=None, f=None, workspace=None,
+                       stream=None):
+    """wri_fwi_adjoint_source: weights (given ``alpha`` or source-free estimates), f += 1/2 sum ||r||^2
+    and the adjoint right-hand sides conj(P^T r) written into ``q_adj`` (one zeroed tensor [nsys, n]
+    per group) from the forward wavefields G in ``groups[g].u``.  Returns (weights complex128 [sum
+    nsys], f tensor [1])."""
+    import torch
+    m = _Marshal(groups, dtype)
+    dev = groups[0].u.device
+    nsys = sum(g.nsys for g in groups)
+    _, cplx = _dtypes(dtype)
+    if len(q_adj) != len(groups):
+        raise ValueError(f"{len(q_adj)} adjoint right-hand sides for {len(groups)} groups")
+    for i, (g, t) in enumerate(zip(groups, q_adj)):
+        _device_tensor(t, f"q_adj {i}", m.device, cplx, g.nsys * g.n)
+    a_in = None
+    if alpha is not None:
+        a_in = torch.view_as_real(alpha.to(torch.complex128).contiguous())
+        _device_tensor(a_in, "alpha", m.device, torch.float64, 2 * nsys)
+    a_out = torch.zeros(nsys, 2, dtype=torch.float64, device=dev)
+    if f is None:
+        f = torch.zeros(1, dtype=torch.float64, device=dev)
+    _device_tensor(f, "f", m.device, torch.float64, 1)
+    ws = _workspace(lib.wri_aux_workspace_size(m.arr, m.n), dev, workspace)
+    qp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in q_adj])
+    _check(lib.wri_fwi_adjoint_source(m.arr, m.n, dtype, _ptr(a_in), _ptr(a_out), qp, _ptr(f), _ptr(ws), ws.numel(),
+                                      _stream(stream)), "wri_fwi_adjoint_source")
+    return torch.view_as_complex(a_out), f
+
+
+def fwi_gradient(groups: Sequence[GroupSpec], dtype: int, alpha, w_adj, grads=None, stream=None):
+    """wri_fwi_gradient: grad += -omega^2 sum Re(w a G w_adj) from the forward wavefields G
+    (``groups[g].u``), the weights and the adjoint solves' wavefields ``w_adj``."""
+    import torch
+    m = _Marshal(groups, dtype)
+    dev = groups[0].u.device
+    _, cplx = _dtypes(dtype)
+    if grads is None:
+        grads = [torch.zeros(g.nz, g.ny, g.nx, dtype=torch.float64, device=dev) for g in groups]
+    a = torch.view_as_real(alpha.to(torch.complex128).contiguous())
+    _device_tensor(a, "alpha", m.device, torch.float64, 2 * sum(g.nsys for g in groups))
+    for i, (g, t, w) in enumerate(zip(groups, grads, w_adj)):
+        _device_tensor(t, f"gradient {i}", m.device, torch.float64, g.n)
+        _device_tensor(w, f"w_adj {i}", m.device, cplx, g.nsys * g.n)
+    wp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in w_adj])
+    gp = (C.c_void_p * len(groups))(*[t.data_ptr() for t in grads])
+    _check(lib.wri_fwi_gradient(m.arr, m.n, dtype, _ptr(a), wp, gp, _stream(stream)), "wri_fwi_gradient")
+    return grads
 
 
 def gradient_noalloc(groups: Sequence[GroupSpec], dtype: int, alpha, grads, f, stream=None):

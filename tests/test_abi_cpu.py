@@ -164,6 +164,24 @@ def test_gradient_refined_needs_a_refined_solve_of_the_same_problem(W):
     assert W.lib.wri_gradient_refined(m2.arr, 1, C.byref(ref), gp, 0x6000, 0x100000, 1 << 40, None) == W.EINVAL
 
 
+def test_general_right_hand_side_and_fwi_calls_validate(W):
+    """lambda = 0 needs a known right-hand side (alpha or q), alpha and q together are an error, and
+    the reduced-FWI calls reject missing outputs before any device work."""
+    o = W.make_opts()
+    assert W.workspace_size([_spec(W, lam=0.0)], o) == 0                               # source-free, no data
+    assert W.workspace_size([_spec(W, lam=0.0, q=_FakeTensor(0x30000))], o) > 0
+    assert W.workspace_size([_spec(W, lam=0.0, alpha=_FakeTensor(0x30000))], o) > 0
+    assert W.workspace_size([_spec(W, alpha=_FakeTensor(0x30000), q=_FakeTensor(0x40000))], o) == 0
+    m = W._Marshal([_spec(W)])
+    qp = (C.c_void_p * 1)(0x5000)
+    assert W.lib.wri_fwi_adjoint_source(m.arr, 1, 0, None, None, qp, 0x6000, 0x1000, 1 << 30, None) == W.EINVAL
+    assert W.lib.wri_fwi_adjoint_source(m.arr, 1, 7, None, 0x7000, qp, 0x6000, 0x1000, 1 << 30, None) == W.EINVAL
+    assert W.lib.wri_fwi_adjoint_source(m.arr, 1, 0, None, 0x7000, qp, 0x6000, 0x1001, 1 << 30, None) == W.EWORKSPACE
+    gp = (C.c_void_p * 1)(0x8000)
+    assert W.lib.wri_fwi_gradient(m.arr, 1, 0, None, qp, gp, None) == W.EINVAL
+    assert W.lib.wri_fwi_gradient(m.arr, 1, 0, 0x9000, (C.c_void_p * 1)(None), gp, None) == W.EINVAL
+
+
 def test_tv_rejects_invalid_arguments(W):
     g = W.WriGrid(20, 18, 16, 3, 10.0, 60.0, 1e-3, 2000.0)
     assert W.lib.wri_tv(C.byref(g), 0x1000, 0.0, 1.0, 0x2000, None, None) == W.EINVAL      # beta = 0
