@@ -119,8 +119,8 @@ typedef struct {
   int32_t warm_start;  /* 1: start from the values in u; 0: start from u = 0 */
   int32_t max_refine;  /* WRI_C64 only: > 0 enables FP64 iterative refinement, at most this
                           many outer corrections; each inner FP32 solve runs to inner_tol, or to
-                          the looser tolerance that already meets refine_tol with 20 % of margin
-                          (a cold start's first inner solve: max(inner_tol, 0.8 refine_tol)) */
+                          the looser tolerance that already meets refine_tol with 5 % of margin
+                          (a cold start's first inner solve: max(inner_tol, 0.95 refine_tol)) */
   double refine_tol;   /* refinement stops when the FP64 relative residual <= refine_tol */
   double inner_tol;    /* relative tolerance of each inner FP32 solve (e.g. 1e-3) */
   int32_t plain;       /* 1: unbatched, unfused baseline (one system at a time, separate

@@ -835,7 +835,7 @@ int solve_refined(const wri_group* groups, int ngroups, const wri_solve_opts* o,
     WRI_CK(cudaMemsetAsync(inner.remaining, 0, 3 * sizeof(int), st));
     Batch r = inner;
     r.flavor = SH_INIT;
-    r.tol = std::max(o->inner_tol, 0.8 * o->refine_tol);
+    r.tol = std::max(o->inner_tol, 0.95 * o->refine_tol);
     WRI_CK(march(4, 4, M_SH, true, P.by, r, st));                  // s = S^H b, r1 = b1, dx = 0
     WRI_CK(cudaMemcpyAsync(slot, inner.remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
     WRI_CK(cudaStreamSynchronize(st));

@@ -159,9 +159,11 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
           sd->status = WRI_SYS_OK;
           sd->gamma = g;
           sd->snorm_ref = rn;
-          // the correction needs no more accuracy than the outer target asks for (20 % of
-          // margin): an inner tolerance tighter than that would only add iterations
-          sd->tol = fmax(b.inner_tol, 0.8 * b.refine_tol * sd->snorm_b / rn);
+          // the correction needs no more accuracy than the outer target asks for, with 5 % of
+          // margin for the drift between the FP32 recurrence and the FP64 residual (measured about
+          // 0.5 % at 1e-2): a tighter inner tolerance would only add iterations, and CGLS's normal
+          // residual can stall for thousands of iterations just below a target
+          sd->tol = fmax(b.inner_tol, 0.95 * b.refine_tol * sd->snorm_b / rn);
           sd->beta = 0.0;
           sd->alpha = 0.0;
           sd->iter = 0;
