@@ -7,7 +7,8 @@ the gradient needs no adjoint solve (Eq. VarG2): the forward pass solves every
 gradient kernel; the backward pass returns ``grad_output * g``.
 
 With complex64 stencils and FP64 refinement (``opts.max_refine > 0``) the refined FP64
-wavefields are kept (``u64``) and the estimate and gradient run FP64 stencils on them.
+wavefields are kept (``u64``), and g and f come from the refinement's FP64 residual
+(``wri.gradient_refined``, no extra stencil pass).
 
 Systems are processed in chunks of at most ``max_resident`` systems per group, so the
 wavefields of one chunk are the only ones held in HBM at any time: when the source batch
@@ -83,14 +84,19 @@ def _evaluate(m: torch.Tensor, prob: Problem, want_grad: bool):
         for b, e in chunks(grp.nsys, prob.max_resident):
             spec = _sub(grp, b, e, mm, u[:e - b], None if u64 is None else u64[:e - b])
             spec.u.zero_()
-            it, rr, st = wri.solve([spec], opts)
+            work = torch.empty(wri.workspace_size([spec], opts), dtype=torch.uint8, device=dev)
+            it, rr, st = wri.solve([spec], opts, workspace=work)
             if bool((st == wri.SYS_NONFINITE).any()):
                 raise FloatingPointError(f"non-finite values in the solves of systems {b}..{e}")
             iters.append(it)
             status.append(st)
             relres.append(rr)
-            a = spec_alpha(spec, dtype)
-            wri.gradient([spec], dtype, a, grads=[scratch_g], f=f)
+            if wide:
+                # the refinement's FP64 residual gives g and f without another stencil pass
+                wri.gradient_refined([spec], opts, work, grads=[scratch_g], f=f)
+            else:
+                a = spec_alpha(spec, dtype)
+                wri.gradient([spec], dtype, a, grads=[scratch_g], f=f)
     prob.stats["iters"] = torch.cat(iters)
     prob.stats["status"] = torch.cat(status)
     prob.stats["relres"] = torch.cat(relres)
