@@ -63,6 +63,52 @@ def test_gradient_allreduce_two_gloo_ranks(tmp_path):
         assert got["f"].item() == 55.0
 
 
+def _sharded_eval_main(rank, world, port, out_dir):
+    """One rank of a sharded WRI evaluation: its share of the systems (parallel_sum.shard) is
+    evaluated (the CPU oracle stands in for the GPU library here), then the one exchange step."""
+    import numpy as np
+    import torch.distributed as dist
+
+    import oracle as O
+    from paper_2410_18429_gb300.parallel_sum import allreduce_gradient, shard
+    from wri_cases import case
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    G = case(nphys=(7, 6, 5), npml=3, nsys=5, seed=21, freq=14.0)
+    b, e = shard(G.nsys, rank, world)
+    off = G.rec_off[b:e + 1]
+    _, _, f, g = O.evaluate(G.spec.shape, G.spec.h, G.omega, G.m, G.spec.npml, G.v_max, G.src[b:e], off - off[0],
+                            G.rec_idx[off[0]:off[-1]], G.d[off[0]:off[-1]], G.lam)
+    gt = [torch.as_tensor(np.asarray(g, dtype=np.float64).reshape(G.spec.shape))]
+    ft = torch.tensor([f], dtype=torch.float64)
+    allreduce_gradient(gt, ft)
+    torch.save({"g": gt[0], "f": ft, "share": (b, e)}, os.path.join(out_dir, f"e{rank}.pt"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_wri_evaluation_two_gloo_ranks(tmp_path):
+    """World size 2 on CPU: 5 systems split 3 + 2 over the ranks, each rank's WRI objective and gradient
+    of its share, one all-reduce: every rank holds the f and g of all 5 systems on one rank."""
+    import torch.multiprocessing as mp
+
+    import oracle as O
+    from wri_cases import case
+    port = _free_port()
+    mp.start_processes(_sharded_eval_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    G = case(nphys=(7, 6, 5), npml=3, nsys=5, seed=21, freq=14.0)
+    _, _, f, g = O.evaluate(G.spec.shape, G.spec.h, G.omega, G.m, G.spec.npml, G.v_max, G.src, G.rec_off, G.rec_idx,
+                            G.d, G.lam)
+    shares = []
+    for r in range(2):
+        got = torch.load(os.path.join(tmp_path, f"e{r}.pt"))
+        shares.append(tuple(got["share"]))
+        assert abs(got["f"].item() - f) <= 1e-12 * abs(f)
+        assert torch.allclose(got["g"].reshape(-1), torch.as_tensor(g), rtol=0, atol=1e-12 * float(np.abs(g).max()))
+    assert shares == [(0, 3), (3, 5)]
+
+
 def test_allreduce_is_identity_without_process_group():
     from paper_2410_18429_gb300.parallel_sum import allreduce_gradient
     g = [torch.ones(3, dtype=torch.float64)]
