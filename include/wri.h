@@ -130,8 +130,9 @@ typedef struct {
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
   int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
-                          1 = z-march kernels only, 2 + c = TMA configuration c (0..19; 9..19
-                          are the warp-specialised kernels); see wri_autotune */
+                          1 = z-march kernels only, 2 + c = TMA configuration c (0..23; 9..23
+                          are the warp-specialised kernels; 22 and 23 update the
+                          iterate every second iteration); see wri_autotune */
   int32_t order;       /* TMA phases: 0 = automatic (6), 1 = tiles of a system consecutive,
                           2 = systems of a tile consecutive, 3 = z-chunk slowest,
                           4 / 5 / 6 = blocks of 4 / 8 / 16 systems, tiles in order */
@@ -266,10 +267,11 @@ WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype
 
 /* Autotuner of the batched solve (an interface outside the paper, which prescribes no
  * kernel configuration).  For a complex64 batch it times `trial_iters` CGLS iterations (>= 2)
- * of every candidate pair (TMA configuration 8, 9, 12, 13, 17 or 18 x work-item order 2, 5 or 6)
+ * of every candidate pair (TMA configuration 8, 9, 12, 13, 17, 18, 20, 21, 22 or 23 x work-item
+ * order 2, 5 or 6)
  * on the caller's own batch, on `stream`, and writes the fastest into opts->kernel and
  * opts->order (other fields unchanged).  With refinement (max_refine > 0) the candidates are
- * the warp-specialised configurations (9, 12, 13, 17, 18), which run its inner solves, and the
+ * the warp-specialised configurations (9, 12, 13, 17, 18, 20-23), which run its inner solves, and the
  * trials are plain CGLS solves.  Candidates whose workspace exceeds ws_bytes are skipped.
  *   - groups[g].u is used as the iterate of the trial solves: its contents are overwritten.
  *   - The choice is cached for the process, keyed by the device, the grids, the system counts

@@ -582,7 +582,9 @@ bool build_tma(const Batch& b, const Plan& P, int* err, int promo, const wri_sol
               encode_vec(&T.map[gi][TM_P1], G.p[1], G, hw, hh, pr) &&
               encode_vec(&T.map[gi][TM_X], G.x, G, WRI_TX, P.by, pr) && encode_vec(&T.map[gi][TM_T1], G.t1, G, hw, hh, pr) &&
               encode_vec(&T.map[gi][TM_R0], G.r1[0], G, hw, hh, pr) && encode_vec(&T.map[gi][TM_R1], G.r1[1], G, hw, hh, pr) &&
-              encode_model(&T.map[gi][TM_M], G.m, G, P.by, pr);
+              encode_model(&T.map[gi][TM_M], G.m, G, P.by, pr) &&
+              encode_vec(&T.map[gi][TM_PC0], G.p[0], G, WRI_TX, P.by, pr) &&
+              encode_vec(&T.map[gi][TM_PC1], G.p[1], G, WRI_TX, P.by, pr);
     if (!ok) return false;
   }
   return true;
@@ -627,13 +629,16 @@ cudaError_t capture_iterations(const Plan& P, const Batch& b1, const Batch& b2, 
 // end.  (Without conditional nodes the graph holds K iterations and the host replays it, reading
 // the counters after every replay.)  The workspace counters are: [0] systems not yet done, [1] the
 // copy-wait error flag, [2] loop bodies run.
-int run_loop(const Plan& P, const Batch& b1, const Batch& b2, int mode2, int K, int max_iter, cudaStream_t st,
+int run_loop(const Plan& P, const Batch& b1_in, const Batch& b2_in, int mode2, int K, int max_iter, cudaStream_t st,
              const TmaSet* tma = nullptr) {
   DevCtx* c = ctx();
   int* slot = poll_slot();
   if (!c || !slot) return WRI_ECUDA;
   const int rb = P.ir ? 4 : P.vbytes / 2;
   const bool use_tma = tma && P.tma_cfg >= 0 && mode2 == M_P2;
+  // iterate updates every second iteration: only the pair configurations' phase-1 kernel does them
+  Batch b1 = b1_in, b2 = b2_in;
+  b1.xpair = b2.xpair = (use_tma && tma_config_xpair(P.tma_cfg)) ? 1 : 0;
   const bool dev_loop = !P.host_loop && device_loop_supported();
   // loop bodies after which the device loop gives up: every system stops by max_iter + 1 iterations
   const int cap_bodies = (max_iter + 2 + K - 1) / K + 2;
@@ -1383,7 +1388,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
     cudaEventDestroy(e0);
     return WRI_ECUDA;
   }
-  static const int kCfgs[] = {8, 9, 12, 13, 17, 18};
+  static const int kCfgs[] = {8, 9, 12, 13, 17, 18, 20, 21, 22, 23};
   static const int kOrders[] = {2, 5, 6};  // systems of a tile consecutive, blocks of 8, blocks of 16
   float best = 0.f;
   int best_kernel = 0, best_order = 0;

@@ -86,7 +86,7 @@ enum Mode : int {
   M_APPLY = 0,  // y = A x (or A^H x); no reduction
   M_SH = 1,     // s = A^H r1 (+ lambda P^T r2 in the finalizer); init of a solve
   M_RES = 2,    // r1 = b1 - Z A x, r2 = lambda (d - P x)
-  M_P1 = 3,     // p = s + beta p_old, t1 = Z A p, x += alpha_prev p_old
+  M_P1 = 3,     // p = s + beta p_old, t1 = Z A p, x += (step of the previous iteration) p_old
   M_P2 = 4,     // r1 = r1_old - alpha t1, s = A^H r1 (CGLS)
   M_GRAD = 6,   // g += omega^2 Re(conj(w u)(A u - a e)), f += 1/2 |A u - a e|^2
 };
@@ -108,6 +108,7 @@ struct SysDev {
   double gamma;      // ||s||^2 of the current normal-equation residual
   double delta;      // ||S p||^2
   double alpha;      // step length of the current iteration
+  double alpha_prev; // step length of the iteration before it (iterate updates every second iteration)
   double beta;       // p = s + beta p
   double snorm_b;    // ||S^H b|| (reference of the relative residual)
   double snorm_ref;  // reference norm of the current (inner) solve
@@ -181,6 +182,8 @@ struct Batch {
                         // consecutive, 2 = z-chunk slowest (the resident wave shares z-slabs),
                         // 3 = blocks of sblock systems, tiles in order, systems fastest in a block
   int sblock;           // systems per block of order 3
+  int xpair;            // 1: phase 1 adds the step of two iterations to x every second iteration
+                        // (warp-specialised pair configurations), 0: one step every iteration
   double tol;           // tolerance of a cold-start solve
   double refine_tol, inner_tol;
   int outer, max_refine, warm;

@@ -58,11 +58,11 @@ static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStr
   return cudaGetLastError();
 }
 
-template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
+template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false, bool XP = false>
 static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   static int occ = -1;
-  const size_t smem = WsLayout<MODE, BY>::bytes(S);
-  auto kern = k_phase_ws<MODE, BY, S, MINB, PW, ER>;
+  const size_t smem = WsLayout<MODE, BY, XP>::bytes(S);
+  auto kern = k_phase_ws<MODE, BY, S, MINB, PW, ER, XP>;
   constexpr int threads = 16 * BY + (PW ? 32 : 0);
   if (occ < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -86,7 +86,7 @@ static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStre
   return cudaGetLastError();
 }
 
-int tma_config_count() { return 20; }
+int tma_config_count() { return 24; }
 
 // config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4) with one node per thread;
 // 4 -> (16, 4), 5 -> (16, 3), 6 -> (8, 6), 7 -> (8, 3; 5 CTAs/SM), 8 -> (8, 4; 4 CTAs/SM) with two
@@ -94,10 +94,15 @@ int tma_config_count() { return 20; }
 // thread): 9 -> (8, 4 stages; 4 CTAs/SM), 10 -> (8, 4; 5 CTAs/SM), 11 -> (8, 6; 3), 12 -> (16, 4; 2),
 // 13 -> (8, 5; 4); without the copy warp (thread 0 issues the copies): 14 -> (8, 4; 5 CTAs/SM),
 // 15 -> (8, 4; 4), 16 -> (16, 4; 3); copy warp and early stage release: 17 -> (8, 4; 4),
-// 18 -> (8, 3; 4), 19 -> (8, 5; 4)
+// 18 -> (8, 3; 4), 19 -> (8, 5; 4); early release with more stages in phase 2 than in phase 1
+// (phase 2 copies two boxes per plane against phase 1's four): 20 -> phase 1 (8, 3; 4) and
+// phase 2 (8, 4; 4), 21 -> phase 1 (8, 3; 4) and phase 2 (8, 5; 4); pair updates (the iterate
+// updated every second iteration): 22 -> as 18, 23 -> as 20
 int tma_config_by(int cfg) {
   return (cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5 || cfg == 12 || cfg == 16) ? 16 : 8;
 }
+
+bool tma_config_xpair(int cfg) { return cfg == 22 || cfg == 23; }
 
 cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   if (b.nitems <= 0) return cudaSuccess;
@@ -155,7 +160,18 @@ cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T,
   WRI_WSE_CASE(M_P2, 18, 8, 3, 4)
   WRI_WSE_CASE(M_P1, 19, 8, 5, 4)
   WRI_WSE_CASE(M_P2, 19, 8, 5, 4)
+  WRI_WSE_CASE(M_P1, 20, 8, 3, 4)
+  WRI_WSE_CASE(M_P2, 20, 8, 4, 4)
+  WRI_WSE_CASE(M_P1, 21, 8, 3, 4)
+  WRI_WSE_CASE(M_P2, 21, 8, 5, 4)
+  WRI_WSE_CASE(M_P2, 22, 8, 3, 4)
+  WRI_WSE_CASE(M_P2, 23, 8, 4, 4)
 #undef WRI_WSE_CASE
+#define WRI_WSP_CASE(M, C_, BY_, S_, MB_) \
+  if (mode == M && cfg == C_) return launch_ws<M, BY_, S_, MB_, true, true, true>(b, T, grid, st);
+  WRI_WSP_CASE(M_P1, 22, 8, 3, 4)
+  WRI_WSP_CASE(M_P1, 23, 8, 3, 4)
+#undef WRI_WSP_CASE
   return cudaErrorInvalidValue;
 }
 

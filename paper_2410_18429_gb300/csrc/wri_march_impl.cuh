@@ -76,17 +76,26 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     const double tot = part + rec;
     if (MODE == M_P1) {
       const double delta = tot;
+      const double a_prev = sd->alpha;
       double alpha = 0.0;
       if (!(delta > 0.0) || !isfinite(delta)) {
         sd->status = isfinite(delta) ? WRI_SYS_BREAKDOWN : WRI_SYS_NONFINITE;
-        sd->state = ST_DONE;
-        atomicSub(b.remaining, 1);
+        if (b.xpair && (sd->iter & 1)) {
+          // pair updates: this odd iteration left the previous step pending; the x-only pass
+          // adds it (step a_prev, direction in the buffer this iteration read p_old from)
+          alpha = a_prev;
+          sd->state = ST_FINISHING;
+        } else {
+          sd->state = ST_DONE;
+          atomicSub(b.remaining, 1);
+        }
       } else {
         alpha = sd->gamma / delta;
       }
       sd->delta = delta;
+      sd->alpha_prev = a_prev;
       sd->alpha = alpha;
-      *bcast = alpha;
+      *bcast = sd->state == ST_ACTIVE ? alpha : 0.0;  // step of the receiver residual (none on breakdown)
     } else if (MODE == M_P2) {
       const double g = tot;
       const int it = sd->iter + 1;
@@ -120,6 +129,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
         sd->gamma = g;
         sd->beta = 0.0;
         sd->alpha = 0.0;
+        sd->alpha_prev = 0.0;
         sd->iter = 0;
         sd->iter_total = 0;
         sd->tol = b.tol;
@@ -166,6 +176,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
           sd->tol = fmax(b.inner_tol, 0.95 * b.refine_tol * sd->snorm_b / rn);
           sd->beta = 0.0;
           sd->alpha = 0.0;
+          sd->alpha_prev = 0.0;
           sd->iter = 0;
           sd->state = ST_ACTIVE;
           atomicAdd(b.remaining, 1);

@@ -22,7 +22,8 @@
 
 namespace wri {
 
-enum TmaMap : int { TM_S = 0, TM_P0, TM_P1, TM_X, TM_T1, TM_R0, TM_R1, TM_M, TM_COUNT };
+// halo boxes of s, p, t1, r1; 32 x BY boxes of x and (pair updates) of p; the model
+enum TmaMap : int { TM_S = 0, TM_P0, TM_P1, TM_X, TM_T1, TM_R0, TM_R1, TM_M, TM_PC0, TM_PC1, TM_COUNT };
 
 struct TmaSet {
   CUtensorMap map[WRI_MAXG][TM_COUNT];
@@ -716,7 +717,7 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
 // All waits are bounded: a time-out raises a CTA-wide abort flag and the error flag of the
 // launch; the other roles see the flag in their waits, every consumer warp still reaches the
 // same named barriers, and the copy warp waits (bounded) for its copies before it exits.
-template <int MODE, int BY>
+template <int MODE, int BY, bool XP = false>
 struct WsLayout {
   static constexpr int HW = WRI_TX + 4;  // 36 columns: x0-2 .. x0+33
   static constexpr int HH = BY + 2;
@@ -726,7 +727,8 @@ struct WsLayout {
   static constexpr int MB = WRI_TX * BY * 4;
   static constexpr int OFF_B = pad(HALO);
   static constexpr int OFF_X = OFF_B + pad(HALO);
-  static constexpr int OFF_M = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);
+  static constexpr int OFF_X2 = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);  // pair updates: p of two iterations back
+  static constexpr int OFF_M = OFF_X2 + (MODE == M_P1 && XP ? pad(CTR) : 0);
   static constexpr int STAGE = OFF_M + pad(MB);
   static size_t bytes(int S) { return 128 + (size_t)S * STAGE + 16 * S; }
 };
@@ -774,14 +776,22 @@ __device__ __forceinline__ float2 fma_c(float c, float2 b, float2 a) {
 // and computes everything of plane k's stencil except the z+1 term (A u is linear in it: the
 // partial value and the z+1 coefficient stay in registers), then releases the stage at once:
 // S - 1 planes of copies stay in flight instead of S - 2.
-template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
+//
+// XP = true ("pair updates", phase 1 only, with b.xpair = 1): the iterate is updated every second
+// iteration, x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1} in iteration k = 2, 4, ...  p_{k-2}
+// still lies in the buffer that iteration k overwrites with p_k (each thread reads its own nodes
+// there before it writes them), so odd iterations read and write no x and even ones read one
+// extra vector: 44 instead of 48 bytes per node-system in phase 1, averaged over two iterations.
+// The x-only pass of a finishing system adds whatever is pending.
+template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false, bool XP = false>
 __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(const __grid_constant__ Batch b,
                                                                              const __grid_constant__ TmaSet T) {
   static_assert(MODE == M_P1 || MODE == M_P2, "the warp-specialised path covers the two CGLS phases");
   static_assert(S >= 3, "two stages are held by the consumers");
   static_assert(PW || !ER, "early release is built with the copy warp");
+  static_assert(!XP || MODE == M_P1, "pair updates change phase 1 only");
   typedef float2 C;
-  typedef WsLayout<MODE, BY> L;
+  typedef WsLayout<MODE, BY, XP> L;
   typedef FirstThreadsSync<16 * BY> CSync;
   constexpr bool CONJ = (MODE == M_P2);
   constexpr int NC = 16 * BY;   // consumer threads: two x-adjacent nodes each
@@ -797,8 +807,8 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
   uint64_t* empty = full + S;
 
   const int tid = threadIdx.x;
-  if ((smem_addr(smem) & 127u) != 0u || (L::OFF_B & 127) || (L::OFF_X & 127) || (L::OFF_M & 127) ||
-      (L::STAGE & 127)) {
+  if ((smem_addr(smem) & 127u) != 0u || (L::OFF_B & 127) || (L::OFF_X & 127) || (L::OFF_X2 & 127) ||
+      (L::OFF_M & 127) || (L::STAGE & 127)) {
     if (tid == 0) atomicExch(T.err, 2);
     return;
   }
@@ -839,8 +849,9 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
       const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
       const bool hasB = (MODE == M_P2) || iter > 0;
       const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
-      const bool hasX = (MODE == M_P1) && iter > 0;
-      const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + L::MB;
+      const bool hasX = (MODE == M_P1) && (XP ? (iter >= 2 && !(iter & 1)) : iter > 0);
+      const bool hasX2 = XP && hasX;
+      const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + (hasX2 ? L::CTR : 0) + L::MB;
       const int count = z1 - z0 + 2;
       for (int q = 0; q < count; ++q, ++fills) {
         const int st = (int)(fills % S);
@@ -863,6 +874,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasX) tma_load_4d(base + L::OFF_X, &T.map[gi][TM_X], x0, y0, kq, sl, &full[st]);
+        if (hasX2) tma_load_4d(base + L::OFF_X2, &T.map[gi][cur ? TM_PC0 : TM_PC1], x0, y0, kq, sl, &full[st]);
         tma_load_3d(base + L::OFF_M, &T.map[gi][TM_M], x0, y0, kq, &full[st]);
       }
     }
@@ -912,17 +924,30 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
       C* X = (C*)G.x + off + col;
       const C* Pc = (const C*)G.p[cur] + off + col;
       const float a = (float)sd->alpha;
+      // pair updates: after an odd number of iterations two steps are pending; the older
+      // direction lies in the other p buffer
+      const bool two = XP && !(iter & 1);
+      const C* Po = (const C*)G.p[cur ^ 1] + off + col;
+      const float a2 = (float)sd->alpha_prev;
       if (own)
         for (int k = z0; k < z1; ++k) {
           const long long q = k * plane;
-          const float4 xv = ld4(X + q), pv = __ldg(reinterpret_cast<const float4*>(Pc + q));
+          float4 xv = ld4(X + q);
+          if (two) {
+            const float4 ov = __ldg(reinterpret_cast<const float4*>(Po + q));
+            xv = make_float4(__fmaf_rn(a2, ov.x, xv.x), __fmaf_rn(a2, ov.y, xv.y), __fmaf_rn(a2, ov.z, xv.z),
+                             __fmaf_rn(a2, ov.w, xv.w));
+          }
+          const float4 pv = __ldg(reinterpret_cast<const float4*>(Pc + q));
           st4(X + q, lo2(xv) + a * lo2(pv), hi2(xv) + a * hi2(pv));
         }
     } else {
       const bool hasB = (MODE == M_P2) || iter > 0;
-      const bool hasX = (MODE == M_P1) && iter > 0;
+      const bool hasX = (MODE == M_P1) && (XP ? (iter >= 2 && !(iter & 1)) : iter > 0);
+      const bool hasX2 = XP && hasX;
       const float coef = (MODE == M_P1) ? (float)sd->beta : -(float)sd->alpha;
       const float xal = (float)sd->alpha;
+      const float xal2 = (float)sd->alpha_prev;
       C* pF = ((MODE == M_P1) ? (C*)G.p[cur ^ 1] : (C*)G.r1[cur ^ 1]) + off + col;
       C* pX = (C*)G.x + off + col;
       C* pO = ((MODE == M_P1) ? (C*)G.t1 : (C*)G.s) + off + col;
@@ -949,13 +974,14 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         if (s_abort) return;
         const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
         const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
-        const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + L::MB;
+        const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + (hasX2 ? L::CTR : 0) + L::MB;
         unsigned char* base = smem + (size_t)st * L::STAGE;
         const int kq = z0 - 1 + q;
         mbar_expect_tx(&full[st], tx_bytes);
         tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasX) tma_load_4d(base + L::OFF_X, &T.map[gi][TM_X], x0, y0, kq, sl, &full[st]);
+        if (hasX2) tma_load_4d(base + L::OFF_X2, &T.map[gi][cur ? TM_PC0 : TM_PC1], x0, y0, kq, sl, &full[st]);
         tma_load_3d(base + L::OFF_M, &T.map[gi][TM_M], x0, y0, kq, &full[st]);
         issued = u + 1;
       };
@@ -1024,7 +1050,13 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
               v0 = fma_c(coef, lo2(bb), v0);
               v1 = fma_c(coef, hi2(bb), v1);
               if (MODE == M_P1 && hasX && mine) {
-                const float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
+                float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
+                if (hasX2) {
+                  // the older step first: the same order as two single updates
+                  const float4 ov = ld4(reinterpret_cast<const C*>(base + L::OFF_X2) + oc);
+                  xv = make_float4(__fmaf_rn(xal2, ov.x, xv.x), __fmaf_rn(xal2, ov.y, xv.y), __fmaf_rn(xal2, ov.z, xv.z),
+                                   __fmaf_rn(xal2, ov.w, xv.w));
+                }
                 st4(pX + po, fma_c(xal, lo2(bb), lo2(xv)), fma_c(xal, hi2(bb), hi2(xv)));
               }
             }
@@ -1163,7 +1195,13 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
             v0 = fma_c(coef, lo2(bb), v0);
             v1 = fma_c(coef, hi2(bb), v1);
             if (MODE == M_P1 && hasX && mine) {
-              const float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
+              float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
+              if (hasX2) {
+                // the older step first: the same order as two single updates
+                const float4 ov = ld4(reinterpret_cast<const C*>(base + L::OFF_X2) + oc);
+                xv = make_float4(__fmaf_rn(xal2, ov.x, xv.x), __fmaf_rn(xal2, ov.y, xv.y), __fmaf_rn(xal2, ov.z, xv.z),
+                                 __fmaf_rn(xal2, ov.w, xv.w));
+              }
               st4(pX + po, fma_c(xal, lo2(bb), lo2(xv)), fma_c(xal, hi2(bb), hi2(xv)));
             }
           }

@@ -88,10 +88,10 @@ def test_fixed_iterations_match_oracle_cgls(W, dtype, tol, source_free):
         assert abs(rr.cpu().numpy()[s] - rr_k) <= max(tol, 1e-6) * rr_k * 10
 
 
-@pytest.mark.parametrize("cfg", list(range(20)))
+@pytest.mark.parametrize("cfg", list(range(24)))
 @pytest.mark.parametrize("source_free", [True, False])
 def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
-    """TMA-pipelined phases (x extent a multiple of 4; configurations 9-19 are the
+    """TMA-pipelined phases (x extent a multiple of 4; configurations 9-23 are the
     warp-specialised kernels): ragged 32 x BY tiles, iterates of k CGLS steps equal the
     oracle's and the z-march kernels' (same tile height)."""
     G = case(nphys=(36, 13, 10), npml=4, nsys=3)
@@ -155,6 +155,36 @@ def test_interior_tiles_tma_match_oracle(W, cfg, order, zsplit):
         # every node, not just the norm: a wrong coefficient on one tile variant shows here
         assert np.max(np.abs(u[s] - x_k)) <= 3e-3 * np.max(np.abs(x_k))
         assert 0 < rr[s] and abs(rr[s] - rr_k) <= 3e-3 * rr_k, (s, rr[s], rr_k)
+
+
+@pytest.mark.parametrize("pair,single", [(22, 18), (23, 20)])
+def test_pair_updates_equal_single_updates(W, pair, single):
+    """Pair configurations update the iterate every second iteration, adding the older step first,
+    so they round exactly like one update per iteration.  On the grid with interior tiles the
+    wavefields, residuals and iteration counts equal the single-update configuration's bit for bit:
+    after an even and an odd number of iterations (one or two steps pending at the end), for solves
+    stopped by their tolerance (systems ending on different iterations), and for the inner solves
+    of an FP64 refinement."""
+    import torch
+    G = _interior_case()
+
+    def run(cfg, **kw):
+        spec = _spec(W, G, 0)
+        if kw.pop("refined", False):
+            spec.u64 = torch.zeros(G.nsys, G.spec.n, dtype=torch.complex128, device="cuda")
+        it, rr, st = W.solve([spec], W.make_opts(dtype=0, kernel=W.KERNEL_TMA(cfg), order=6, **kw))
+        u = (spec.u64 if spec.u64 is not None else spec.u).cpu().numpy()
+        return u, rr.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+
+    cases = [dict(tol=0.0, max_iter=24), dict(tol=0.0, max_iter=25), dict(tol=1e-3, max_iter=100000),
+             dict(tol=1e-6, max_iter=100000, max_refine=3, refine_tol=1e-6, inner_tol=1e-3, refined=True)]
+    for kw in cases:
+        a, b = run(pair, **dict(kw)), run(single, **dict(kw))
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3]), (kw, a[2], b[2], a[3], b[3])
+        assert np.array_equal(a[0], b[0]), (kw, rel(a[0], b[0]))
+        assert np.array_equal(a[1], b[1]), (kw, a[1], b[1])
+        if kw["tol"] > 0:
+            assert a[3].tolist() == [W.SYS_OK] * G.nsys, (kw, a[3])
 
 
 @pytest.mark.parametrize("dtype,tol", [(1, 1e-10), (0, 3e-4)])
@@ -472,7 +502,7 @@ def test_autotune_choice_solves_like_default_and_is_cached(W):
     s1, s2 = _spec(W, G1, 0), _spec(W, G2, 0)
     base = W.make_opts(tol=0.0, max_iter=20, dtype=0)
     tuned = W.autotune([s1, s2], base, trial_iters=6)
-    assert tuned.kernel in [2 + c for c in (8, 9, 12, 13, 17, 18)] and tuned.order in (2, 5, 6)
+    assert tuned.kernel in [2 + c for c in (8, 9, 12, 13, 17, 18, 20, 21, 22, 23)] and tuned.order in (2, 5, 6)
     s1.u.fill_(3.0)
     again = W.autotune([s1, s2], base, trial_iters=6)
     assert (again.kernel, again.order) == (tuned.kernel, tuned.order)
