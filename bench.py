@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = "WRI gradient src·freq/s at 128³ (GPt·iter/s, % HBM roofline) vs plain path"
 UNIT = "src·freq/s"
 BYTES_PER_NODE_SYS = 80.0  # one CGLS iteration, per node and system: phase 1 48 B + phase 2 32 B (c64)
+# pair-update configurations: x read and written every second iteration, plus one extra p read then:
+# phase 1 (32 + 56) / 2 = 44 B
+PAIR_CONFIGS = (22, 23)
+BYTES_PER_NODE_SYS_PAIR = 76.0
 MODEL_BYTES = 8.0          # m (float32) read by both phases, per node of a group, shared by its systems
 K_POLL = 2                 # CG iterations per body of the iteration graph's device-side loop
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cg_iteration_traffic.json")
@@ -81,6 +85,12 @@ def workload_name(args):
         return "c4-batch-small"
     base = "c4-batch: {} src x {{3 Hz 84^3, 5 Hz 116^3, 8 Hz 148^3}}".format(args.nsrc)
     return base if args.only_group < 0 else base + f" (group {args.only_group} only)"
+
+
+def bytes_per_node_sys(opts):
+    """Algorithmic bytes of one CGLS iteration per node and system for the configuration of opts."""
+    k = int(opts.kernel)
+    return BYTES_PER_NODE_SYS_PAIR if k >= 2 and k - 2 in PAIR_CONFIGS else BYTES_PER_NODE_SYS
 
 
 def phase_kernel_name(opts):
@@ -285,7 +295,7 @@ def run_group_sweep(args):
         ta = min(timed(20) for _ in range(2))
         tb = min(timed(80) for _ in range(2))
         t_iter = (tb - ta) / 60.0
-        alg = n * (BYTES_PER_NODE_SYS * nb + MODEL_BYTES)
+        alg = n * (bytes_per_node_sys(base) * nb + MODEL_BYTES)
         print(json.dumps({"group_sweep": nb, "grid": f"{g0.spec.nx}x{g0.spec.ny}x{g0.spec.nz}",
                           "ms_per_iter": t_iter * 1e3, "us_per_system_iter": t_iter / nb * 1e6,
                           "gpt_iter_s": nb * n / t_iter / 1e9, "hbm_gbs": alg / t_iter / 1e9,
@@ -488,7 +498,7 @@ def main():
     t_hi = min(timed_solve(iters_done) for _ in range(2))
     t_lo = min(timed_solve(lo_iters) for _ in range(2))
     t_iter = (t_hi - t_lo) / (iters_done - lo_iters)
-    alg_bytes = node_sys * BYTES_PER_NODE_SYS + sum(g.spec.n for g in groups) * MODEL_BYTES
+    alg_bytes = node_sys * bytes_per_node_sys(opts) + sum(g.spec.n for g in groups) * MODEL_BYTES
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -938,8 +938,10 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
             xv = make_float4(__fmaf_rn(a2, ov.x, xv.x), __fmaf_rn(a2, ov.y, xv.y), __fmaf_rn(a2, ov.z, xv.z),
                              __fmaf_rn(a2, ov.w, xv.w));
           }
+          // explicit fma (as in the iteration's own update): the rounding must not depend on how
+          // the compiler contracts this instantiation
           const float4 pv = __ldg(reinterpret_cast<const float4*>(Pc + q));
-          st4(X + q, lo2(xv) + a * lo2(pv), hi2(xv) + a * hi2(pv));
+          st4(X + q, fma_c(a, lo2(pv), lo2(xv)), fma_c(a, hi2(pv), hi2(xv)));
         }
     } else {
       const bool hasB = (MODE == M_P2) || iter > 0;

@@ -181,7 +181,8 @@ def test_pair_updates_equal_single_updates(W, pair, single):
     for kw in cases:
         a, b = run(pair, **dict(kw)), run(single, **dict(kw))
         assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3]), (kw, a[2], b[2], a[3], b[3])
-        assert np.array_equal(a[0], b[0]), (kw, rel(a[0], b[0]))
+        diff = np.flatnonzero(a[0].ravel() != b[0].ravel())
+        assert diff.size == 0, (kw, diff.size, diff[:8], rel(a[0], b[0]))
         assert np.array_equal(a[1], b[1]), (kw, a[1], b[1])
         if kw["tol"] > 0:
             assert a[3].tolist() == [W.SYS_OK] * G.nsys, (kw, a[3])
