@@ -58,27 +58,30 @@ static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStr
   return cudaGetLastError();
 }
 
-template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false, bool XP = false>
+template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
 static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
-  static int occ = -1;
-  const size_t smem = WsLayout<MODE, BY, XP>::bytes(S);
-  auto kern = k_phase_ws<MODE, BY, S, MINB, PW, ER, XP>;
+  static int occ[2] = {-1, -1};  // without / with the pair-update box
+  const int xp = (MODE == M_P1 && b.xpair) ? 1 : 0;
+  const size_t smem = WsLayout<MODE, BY>::bytes(S, xp != 0);
+  auto kern = k_phase_ws<MODE, BY, S, MINB, PW, ER>;
   constexpr int threads = 16 * BY + (PW ? 32 : 0);
-  if (occ < 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (occ[xp] < 0) {
+    // the attribute covers the larger of the two sizes
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)WsLayout<MODE, BY>::bytes(S, true));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem);
     if (e != cudaSuccess) return e;
-    occ = n > 0 ? n : 1;
+    occ[xp] = n > 0 ? n : 1;
   }
   if (grid <= 0) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long g = (long long)sms * occ;
+    const long long g = (long long)sms * occ[xp];
     grid = (int)(g < b.nitems ? g : b.nitems);
     if (grid < 1) grid = 1;
   }
@@ -164,14 +167,12 @@ cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T,
   WRI_WSE_CASE(M_P2, 20, 8, 4, 4)
   WRI_WSE_CASE(M_P1, 21, 8, 3, 4)
   WRI_WSE_CASE(M_P2, 21, 8, 5, 4)
+  // pair updates: the same kernels as 18 and 20, with b.xpair set by the caller
+  WRI_WSE_CASE(M_P1, 22, 8, 3, 4)
   WRI_WSE_CASE(M_P2, 22, 8, 3, 4)
+  WRI_WSE_CASE(M_P1, 23, 8, 3, 4)
   WRI_WSE_CASE(M_P2, 23, 8, 4, 4)
 #undef WRI_WSE_CASE
-#define WRI_WSP_CASE(M, C_, BY_, S_, MB_) \
-  if (mode == M && cfg == C_) return launch_ws<M, BY_, S_, MB_, true, true, true>(b, T, grid, st);
-  WRI_WSP_CASE(M_P1, 22, 8, 3, 4)
-  WRI_WSP_CASE(M_P1, 23, 8, 3, 4)
-#undef WRI_WSP_CASE
   return cudaErrorInvalidValue;
 }
 

@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(16 * BY, MINB) k_phase_tma2(const __grid_const
 // All waits are bounded: a time-out raises a CTA-wide abort flag and the error flag of the
 // launch; the other roles see the flag in their waits, every consumer warp still reaches the
 // same named barriers, and the copy warp waits (bounded) for its copies before it exits.
-template <int MODE, int BY, bool XP = false>
+template <int MODE, int BY>
 struct WsLayout {
   static constexpr int HW = WRI_TX + 4;  // 36 columns: x0-2 .. x0+33
   static constexpr int HH = BY + 2;
@@ -727,10 +727,12 @@ struct WsLayout {
   static constexpr int MB = WRI_TX * BY * 4;
   static constexpr int OFF_B = pad(HALO);
   static constexpr int OFF_X = OFF_B + pad(HALO);
-  static constexpr int OFF_X2 = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);  // pair updates: p of two iterations back
-  static constexpr int OFF_M = OFF_X2 + (MODE == M_P1 && XP ? pad(CTR) : 0);
+  static constexpr int OFF_M = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);
   static constexpr int STAGE = OFF_M + pad(MB);
-  static size_t bytes(int S) { return 128 + (size_t)S * STAGE + 16 * S; }
+  // pair updates (phase 1): p of two iterations back, in a box appended to each stage
+  static constexpr int OFF_X2 = STAGE;
+  static constexpr int X2 = (MODE == M_P1) ? pad(CTR) : 0;
+  static size_t bytes(int S, bool xpair) { return 128 + (size_t)S * (STAGE + (xpair ? X2 : 0)) + 16 * S; }
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -777,21 +779,24 @@ __device__ __forceinline__ float2 fma_c(float c, float2 b, float2 a) {
 // partial value and the z+1 coefficient stay in registers), then releases the stage at once:
 // S - 1 planes of copies stay in flight instead of S - 2.
 //
-// XP = true ("pair updates", phase 1 only, with b.xpair = 1): the iterate is updated every second
+// b.xpair = 1 ("pair updates", phase 1 only): the iterate is updated every second
 // iteration, x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1} in iteration k = 2, 4, ...  p_{k-2}
 // still lies in the buffer that iteration k overwrites with p_k (each thread reads its own nodes
 // there before it writes them), so odd iterations read and write no x and even ones read one
 // extra vector: 44 instead of 48 bytes per node-system in phase 1, averaged over two iterations.
-// The x-only pass of a finishing system adds whatever is pending.
-template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false, bool XP = false>
+// The x-only pass of a finishing system adds whatever is pending.  A run-time switch of the same
+// kernel, so the stencil and the reductions are the same machine code with and without it; each
+// stage then holds one more 32 x BY box (the launch sizes the shared memory for it).
+template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
 __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(const __grid_constant__ Batch b,
                                                                              const __grid_constant__ TmaSet T) {
   static_assert(MODE == M_P1 || MODE == M_P2, "the warp-specialised path covers the two CGLS phases");
   static_assert(S >= 3, "two stages are held by the consumers");
   static_assert(PW || !ER, "early release is built with the copy warp");
-  static_assert(!XP || MODE == M_P1, "pair updates change phase 1 only");
   typedef float2 C;
-  typedef WsLayout<MODE, BY, XP> L;
+  typedef WsLayout<MODE, BY> L;
+  const bool XP = (MODE == M_P1) && b.xpair != 0;
+  const int SB = L::STAGE + (XP ? L::X2 : 0);  // bytes of one stage
   typedef FirstThreadsSync<16 * BY> CSync;
   constexpr bool CONJ = (MODE == M_P2);
   constexpr int NC = 16 * BY;   // consumer threads: two x-adjacent nodes each
@@ -803,12 +808,12 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
   __shared__ volatile int s_abort;
   __shared__ C xs_tab[WRI_TX], xh_tab[WRI_TX + 1], ys_tab[BY], yh_tab[BY + 1];
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::STAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
   uint64_t* empty = full + S;
 
   const int tid = threadIdx.x;
   if ((smem_addr(smem) & 127u) != 0u || (L::OFF_B & 127) || (L::OFF_X & 127) || (L::OFF_X2 & 127) ||
-      (L::OFF_M & 127) || (L::STAGE & 127)) {
+      (L::OFF_M & 127) || (L::STAGE & 127) || (SB & 127)) {
     if (tid == 0) atomicExch(T.err, 2);
     return;
   }
@@ -868,7 +873,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         // test hook (off unless the caller asks): this fill is never issued, so its "full" barrier
         // never completes and the consumers' bounded wait for it runs out
         if (blockIdx.x == 0 && (int)fills == T.withhold) continue;
-        unsigned char* base = smem + (size_t)st * L::STAGE;
+        unsigned char* base = smem + (size_t)st * SB;
         const int kq = z0 - 1 + q;
         mbar_expect_tx(&full[st], tx_bytes);
         tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
@@ -977,7 +982,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
         const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
         const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + (hasX2 ? L::CTR : 0) + L::MB;
-        unsigned char* base = smem + (size_t)st * L::STAGE;
+        unsigned char* base = smem + (size_t)st * SB;
         const int kq = z0 - 1 + q;
         mbar_expect_tx(&full[st], tx_bytes);
         tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
@@ -1039,7 +1044,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
           }
           C v0 = czero<float>(), v1 = v0;
           if (ok) {
-            const unsigned char* base = smem + (size_t)st * L::STAGE;
+            const unsigned char* base = smem + (size_t)st * SB;
             const C* A = reinterpret_cast<const C*>(base);
             const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
             const int kq = z0 - 1 + q;
@@ -1184,7 +1189,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         C v0 = czero<float>(), v1 = v0;
         float2 m_new = make_float2(0.f, 0.f);
         if (ok) {
-          const unsigned char* base = smem + (size_t)st * L::STAGE;
+          const unsigned char* base = smem + (size_t)st * SB;
           const C* A = reinterpret_cast<const C*>(base);
           const C* B = reinterpret_cast<const C*>(base + L::OFF_B);
           const int kq = z0 - 1 + q;
@@ -1213,7 +1218,7 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
             // stencil of plane kp = kq - 1: z neighbours from registers, in-plane neighbours
             // formed from the copy boxes of plane kp
             const int kp = kq - 1;
-            const unsigned char* bp = smem + (size_t)((u - 1) % S) * L::STAGE;
+            const unsigned char* bp = smem + (size_t)((u - 1) % S) * SB;
             const C* Ap = reinterpret_cast<const C*>(bp);
             const C* Bp = reinterpret_cast<const C*>(bp + L::OFF_B);
             C l = Ap[o - 1], r = Ap[o + 2];
