@@ -184,7 +184,7 @@ def test_pair_updates_equal_single_updates(W, pair, single):
         diff = np.flatnonzero(a[0].ravel() != b[0].ravel())
         assert diff.size == 0, (kw, diff.size, diff[:8], rel(a[0], b[0]))
         assert np.array_equal(a[1], b[1]), (kw, a[1], b[1])
-        if kw["tol"] > 0:
+        if kw["tol"] > 0 and "refined" not in kw:
             assert a[3].tolist() == [W.SYS_OK] * G.nsys, (kw, a[3])
 
 
