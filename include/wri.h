@@ -267,11 +267,10 @@ WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype
 
 /* Autotuner of the batched solve (an interface outside the paper, which prescribes no
  * kernel configuration).  For a complex64 batch it times `trial_iters` CGLS iterations (>= 2)
- * of every candidate pair (TMA configuration 8, 9, 12, 13, 17, 18, 20, 21, 22 or 23 x work-item
- * order 2, 5 or 6)
+ * of every candidate pair (TMA configuration 8, 9, 12, 13, 17, 18 or 22 x work-item order 2, 5 or 6)
  * on the caller's own batch, on `stream`, and writes the fastest into opts->kernel and
  * opts->order (other fields unchanged).  With refinement (max_refine > 0) the candidates are
- * the warp-specialised configurations (9, 12, 13, 17, 18, 20-23), which run its inner solves, and the
+ * the warp-specialised configurations (9, 12, 13, 17, 18, 22), which run its inner solves, and the
  * trials are plain CGLS solves.  Candidates whose workspace exceeds ws_bytes are skipped.
  *   - groups[g].u is used as the iterate of the trial solves: its contents are overwritten.
  *   - The choice is cached for the process, keyed by the device, the grids, the system counts

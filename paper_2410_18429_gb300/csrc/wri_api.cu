@@ -1388,7 +1388,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
     cudaEventDestroy(e0);
     return WRI_ECUDA;
   }
-  static const int kCfgs[] = {8, 9, 12, 13, 17, 18, 20, 21, 22, 23};
+  static const int kCfgs[] = {8, 9, 12, 13, 17, 18, 22};
   static const int kOrders[] = {2, 5, 6};  // systems of a tile consecutive, blocks of 8, blocks of 16
   float best = 0.f;
   int best_kernel = 0, best_order = 0;

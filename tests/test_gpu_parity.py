@@ -503,7 +503,7 @@ def test_autotune_choice_solves_like_default_and_is_cached(W):
     s1, s2 = _spec(W, G1, 0), _spec(W, G2, 0)
     base = W.make_opts(tol=0.0, max_iter=20, dtype=0)
     tuned = W.autotune([s1, s2], base, trial_iters=6)
-    assert tuned.kernel in [2 + c for c in (8, 9, 12, 13, 17, 18, 20, 21, 22, 23)] and tuned.order in (2, 5, 6)
+    assert tuned.kernel in [2 + c for c in (8, 9, 12, 13, 17, 18, 22)] and tuned.order in (2, 5, 6)
     s1.u.fill_(3.0)
     again = W.autotune([s1, s2], base, trial_iters=6)
     assert (again.kernel, again.order) == (tuned.kernel, tuned.order)
