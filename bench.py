@@ -33,10 +33,9 @@ sys.path.insert(0, ROOT)
 METRIC = "WRI gradient src·freq/s at 128³ (GPt·iter/s, % HBM roofline) vs plain path"
 UNIT = "src·freq/s"
 BYTES_PER_NODE_SYS = 80.0  # one CGLS iteration, per node and system: phase 1 48 B + phase 2 32 B (c64)
-# pair-update configurations: x read and written every second iteration, plus one extra p read then:
-# phase 1 (32 + 56) / 2 = 44 B
-PAIR_CONFIGS = (22, 23)
-BYTES_PER_NODE_SYS_PAIR = 76.0
+# grouped-update configurations: x read and written every m-th iteration, with m - 1 extra p reads
+# then: phase 1 (m 32 + 16 + 8 (m - 1)) / m = 44 B (m = 2) or 42 B (m = 4)
+XSTEPS = {22: 2, 23: 2, 24: 4}
 MODEL_BYTES = 8.0          # m (float32) read by both phases, per node of a group, shared by its systems
 K_POLL = 2                 # CG iterations per body of the iteration graph's device-side loop
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cg_iteration_traffic.json")
@@ -90,7 +89,8 @@ def workload_name(args):
 def bytes_per_node_sys(opts):
     """Algorithmic bytes of one CGLS iteration per node and system for the configuration of opts."""
     k = int(opts.kernel)
-    return BYTES_PER_NODE_SYS_PAIR if k >= 2 and k - 2 in PAIR_CONFIGS else BYTES_PER_NODE_SYS
+    m = XSTEPS.get(k - 2, 1) if k >= 2 else 1
+    return BYTES_PER_NODE_SYS - 16.0 + (16.0 + 8.0 * (m - 1)) / m
 
 
 def phase_kernel_name(opts):

@@ -130,9 +130,9 @@ typedef struct {
   int32_t tile;        /* tile configuration (0 = autotuned / default, see wri_tile_count) */
   int32_t zsplit;      /* z-chunks per tile column (0 = chosen from the batch size) */
   int32_t kernel;      /* 0 = automatic (TMA-pipelined phases when the batch allows them),
-                          1 = z-march kernels only, 2 + c = TMA configuration c (0..23; 9..23
+                          1 = z-march kernels only, 2 + c = TMA configuration c (0..24; 9..24
                           are the warp-specialised kernels; 22 and 23 update the
-                          iterate every second iteration); see wri_autotune */
+                          iterate every second iteration, 24 every fourth); see wri_autotune */
   int32_t order;       /* TMA phases: 0 = automatic (6), 1 = tiles of a system consecutive,
                           2 = systems of a tile consecutive, 3 = z-chunk slowest,
                           4 / 5 / 6 = blocks of 4 / 8 / 16 systems, tiles in order */
@@ -162,7 +162,9 @@ WRI_API int wri_apply_AH(const wri_grid* grid, int dtype, const void* m, int nsy
                  wri_stream_t stream);
 
 /* Bytes of device workspace wri_solve_batch needs for these groups and options
- * (0 on invalid arguments).  The workspace must be 256-byte aligned. */
+ * (0 on invalid arguments).  The workspace must be 256-byte aligned.  With opts->kernel = 0
+ * (automatic) it also covers the four search-direction vectors per system of TMA configuration
+ * 24, so that a workspace sized before wri_autotune fits every configuration it may choose. */
 WRI_API size_t wri_workspace_size(const wri_group* groups, int ngroups, const wri_solve_opts* opts);
 
 /* Solve every system of every group (the LSQR/CG solve of Eq. SimpObj, Algorithm 1
@@ -267,10 +269,11 @@ WRI_API int wri_gradient_noalloc(const wri_group* groups, int ngroups, int dtype
 
 /* Autotuner of the batched solve (an interface outside the paper, which prescribes no
  * kernel configuration).  For a complex64 batch it times `trial_iters` CGLS iterations (>= 2)
- * of every candidate pair (TMA configuration 8, 9, 12, 13, 17, 18 or 22 x work-item order 2, 5 or 6)
+ * of every candidate pair (TMA configuration 8, 9, 12, 13, 17, 18, 22 or 24 x work-item order 2, 5
+ * or 6)
  * on the caller's own batch, on `stream`, and writes the fastest into opts->kernel and
  * opts->order (other fields unchanged).  With refinement (max_refine > 0) the candidates are
- * the warp-specialised configurations (9, 12, 13, 17, 18, 22), which run its inner solves, and the
+ * the warp-specialised configurations (9, 12, 13, 17, 18, 22, 24), which run its inner solves, and the
  * trials are plain CGLS solves.  Candidates whose workspace exceeds ws_bytes are skipped.
  *   - groups[g].u is used as the iterate of the trial solves: its contents are overwritten.
  *   - The choice is cached for the process, keyed by the device, the grids, the system counts

@@ -173,7 +173,8 @@ struct Plan {
   size_t off_r2_64 = 0, off_r2_in = 0;  // refinement: FP64 receiver residual master, complex64 inner r2
   size_t aux_total = 0, total = 0;
   GroupDev g[WRI_MAXG];
-  size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][2], v_s[WRI_MAXG], v_t1[WRI_MAXG];
+  size_t v_r1[WRI_MAXG][2], v_p[WRI_MAXG][4], v_s[WRI_MAXG], v_t1[WRI_MAXG];
+  int pslots = 2;  // search-direction slots: 4 when the phases may update x every fourth iteration
   size_t v_x32[WRI_MAXG], v_x64[WRI_MAXG], v_r64[WRI_MAXG], v_q64[WRI_MAXG], v_g32[WRI_MAXG], v_rmap[WRI_MAXG];
   size_t off_ztab[WRI_MAXG], off_ztab64[WRI_MAXG];  // z-coefficient tables (FP32, FP64) per group
   size_t off_rmask[WRI_MAXG], off_rcol[WRI_MAXG], rmask_bytes[WRI_MAXG], rcol_bytes[WRI_MAXG];
@@ -230,6 +231,9 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
       // the refinement's inner phase 2 adds S^H r64, which only the warp-specialised kernels do
       if (P.ir && P.tma_cfg < kFirstWsCfg) P.tma_cfg = kDefaultTmaCfg;
       P.by = tma_config_by(P.tma_cfg);
+      // a ring of four directions for the configurations that update x every fourth iteration; the
+      // automatic choice reserves it too, so that wri_autotune may pick them in the same workspace
+      P.pslots = (o->kernel == 0 || tma_config_xsteps(P.tma_cfg) == 4) ? 4 : 2;
     }
   }
   P.vbytes = (o->dtype == WRI_C128) ? 16 : 8;
@@ -291,6 +295,11 @@ void plan_solve(const wri_group* groups, int ngroups, const wri_solve_opts* o, P
     P.v_r1[gi][1] = off; off += vb;
     P.v_p[gi][0] = off; off += vb;
     P.v_p[gi][1] = off; off += vb;
+    P.v_p[gi][2] = P.v_p[gi][3] = 0;
+    if (P.pslots == 4) {
+      P.v_p[gi][2] = off; off += vb;
+      P.v_p[gi][3] = off; off += vb;
+    }
     P.v_s[gi] = off; off += vb;
     P.v_t1[gi] = off; off += vb;
     P.v_x32[gi] = P.v_x64[gi] = P.v_r64[gi] = P.v_q64[gi] = P.v_g32[gi] = P.v_rmap[gi] = 0;
@@ -488,6 +497,8 @@ Batch solver_batch(const wri_group* groups, const Plan& P, char* ws, bool inner_
     G.r1[1] = ws + P.v_r1[gi][1];
     G.p[0] = ws + P.v_p[gi][0];
     G.p[1] = ws + P.v_p[gi][1];
+    G.p[2] = P.pslots == 4 ? ws + P.v_p[gi][2] : nullptr;
+    G.p[3] = P.pslots == 4 ? ws + P.v_p[gi][3] : nullptr;
     G.s = ws + P.v_s[gi];
     G.t1 = ws + P.v_t1[gi];
     G.x = (P.ir && inner_view) ? (void*)(ws + P.v_x32[gi]) : U.u;
@@ -585,6 +596,10 @@ bool build_tma(const Batch& b, const Plan& P, int* err, int promo, const wri_sol
               encode_model(&T.map[gi][TM_M], G.m, G, P.by, pr) &&
               encode_vec(&T.map[gi][TM_PC0], G.p[0], G, WRI_TX, P.by, pr) &&
               encode_vec(&T.map[gi][TM_PC1], G.p[1], G, WRI_TX, P.by, pr);
+    for (int slot = 2; slot < 4 && ok; ++slot)
+      if (G.p[slot])
+        ok = encode_vec(&T.map[gi][TM_P0 + slot], G.p[slot], G, hw, hh, pr) &&
+             encode_vec(&T.map[gi][TM_PC0 + slot], G.p[slot], G, WRI_TX, P.by, pr);
     if (!ok) return false;
   }
   return true;
@@ -636,9 +651,12 @@ int run_loop(const Plan& P, const Batch& b1_in, const Batch& b2_in, int mode2, i
   if (!c || !slot) return WRI_ECUDA;
   const int rb = P.ir ? 4 : P.vbytes / 2;
   const bool use_tma = tma && P.tma_cfg >= 0 && mode2 == M_P2;
-  // iterate updates every second iteration: only the pair configurations' phase-1 kernel does them
+  // iterate updates every m-th iteration: only the grouped-update configurations' phase-1 kernel
+  // does them (m = 4 needs the four direction slots)
   Batch b1 = b1_in, b2 = b2_in;
-  b1.xpair = b2.xpair = (use_tma && tma_config_xpair(P.tma_cfg)) ? 1 : 0;
+  int xs = use_tma ? tma_config_xsteps(P.tma_cfg) : 1;
+  if (xs == 4 && !b1.g[0].p[2]) return WRI_EINVAL;
+  b1.xsteps = b2.xsteps = xs;
   const bool dev_loop = !P.host_loop && device_loop_supported();
   // loop bodies after which the device loop gives up: every system stops by max_iter + 1 iterations
   const int cap_bodies = (max_iter + 2 + K - 1) / K + 2;
@@ -1388,7 +1406,7 @@ int wri_autotune(const wri_group* groups, int ngroups, wri_solve_opts* opts, int
     cudaEventDestroy(e0);
     return WRI_ECUDA;
   }
-  static const int kCfgs[] = {8, 9, 12, 13, 17, 18, 22};
+  static const int kCfgs[] = {8, 9, 12, 13, 17, 18, 22, 24};
   static const int kOrders[] = {2, 5, 6};  // systems of a tile consecutive, blocks of 8, blocks of 16
   float best = 0.f;
   int best_kernel = 0, best_order = 0;

@@ -108,7 +108,8 @@ struct SysDev {
   double gamma;      // ||s||^2 of the current normal-equation residual
   double delta;      // ||S p||^2
   double alpha;      // step length of the current iteration
-  double alpha_prev; // step length of the iteration before it (iterate updates every second iteration)
+  double alpha_hist[3];  // step lengths of the three iterations before it, newest first (iterate
+                         // updated every m-th iteration: the steps not yet added to x)
   double beta;       // p = s + beta p
   double snorm_b;    // ||S^H b|| (reference of the relative residual)
   double snorm_ref;  // reference norm of the current (inner) solve
@@ -145,7 +146,8 @@ struct GroupDev {
   int q_double;             // 1 if q is double2 (complex128 problems), 0 if float2
   void* x;                  // [nsys][n] iterate (dtype of the stencil)
   void* r1[2];              // [nsys][n] data-space residual, ping-pong
-  void* p[2];               // [nsys][n] search direction, ping-pong
+  void* p[4];               // [nsys][n] search direction: p_j in slot (j + 1) mod R, R = 2 (ping-pong) or
+                            // 4 (iterate updated every fourth iteration; slots 2, 3 null otherwise)
   void* s;                  // [nsys][n] normal-equation residual S^H r
   void* t1;                 // [nsys][n] Z A p
   void* x64;                // [nsys][n] double2 refinement master of the solution (or null)
@@ -182,13 +184,19 @@ struct Batch {
                         // consecutive, 2 = z-chunk slowest (the resident wave shares z-slabs),
                         // 3 = blocks of sblock systems, tiles in order, systems fastest in a block
   int sblock;           // systems per block of order 3
-  int xpair;            // 1: phase 1 adds the step of two iterations to x every second iteration
-                        // (warp-specialised pair configurations), 0: one step every iteration
+  int xsteps;           // m: phase 1 adds the steps of m iterations to x every m-th iteration (m = 2, 4:
+                        // the warp-specialised grouped-update configurations; 0 or 1: every iteration)
   double tol;           // tolerance of a cold-start solve
   double refine_tol, inner_tol;
   int outer, max_refine, warm;
   GroupDev g[WRI_MAXG];
 };
+
+// steps per iterate update (1, 2 or 4) and the p ring of a batch
+__host__ __device__ __forceinline__ int xsteps_of(const Batch& b) { return b.xsteps > 1 ? b.xsteps : 1; }
+__host__ __device__ __forceinline__ int pring_of(const Batch& b) { return b.xsteps == 4 ? 4 : 2; }
+// slot of p_j
+__host__ __device__ __forceinline__ int pslot(const Batch& b, int j) { return (j + 1) & (pring_of(b) - 1); }
 
 // (system, tile) of a work item of group G under the batch's work order
 __device__ __forceinline__ void item_coords(const Batch& b, const GroupDev& G, long long local, int& sl, int& tile) {

@@ -60,15 +60,15 @@ static cudaError_t launch_two(const Batch& b, const TmaSet& T, int grid, cudaStr
 
 template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
 static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
-  static int occ[2] = {-1, -1};  // without / with the pair-update box
-  const int xp = (MODE == M_P1 && b.xpair) ? 1 : 0;
-  const size_t smem = WsLayout<MODE, BY>::bytes(S, xp != 0);
+  static int occ[4] = {-1, -1, -1, -1};  // by the number of extra update boxes per stage
+  const int xp = (MODE == M_P1) ? xsteps_of(b) - 1 : 0;
+  const size_t smem = WsLayout<MODE, BY>::bytes(S, xp);
   auto kern = k_phase_ws<MODE, BY, S, MINB, PW, ER>;
   constexpr int threads = 16 * BY + (PW ? 32 : 0);
   if (occ[xp] < 0) {
     // the attribute covers the larger of the two sizes
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)WsLayout<MODE, BY>::bytes(S, true));
+                                         (int)WsLayout<MODE, BY>::bytes(S, 3));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
@@ -89,7 +89,7 @@ static cudaError_t launch_ws(const Batch& b, const TmaSet& T, int grid, cudaStre
   return cudaGetLastError();
 }
 
-int tma_config_count() { return 24; }
+int tma_config_count() { return 25; }
 
 // config: 0 -> (BY 8, 4 stages), 1 -> (8, 6), 2 -> (16, 3), 3 -> (16, 4) with one node per thread;
 // 4 -> (16, 4), 5 -> (16, 3), 6 -> (8, 6), 7 -> (8, 3; 5 CTAs/SM), 8 -> (8, 4; 4 CTAs/SM) with two
@@ -99,13 +99,13 @@ int tma_config_count() { return 24; }
 // 15 -> (8, 4; 4), 16 -> (16, 4; 3); copy warp and early stage release: 17 -> (8, 4; 4),
 // 18 -> (8, 3; 4), 19 -> (8, 5; 4); early release with more stages in phase 2 than in phase 1
 // (phase 2 copies two boxes per plane against phase 1's four): 20 -> phase 1 (8, 3; 4) and
-// phase 2 (8, 4; 4), 21 -> phase 1 (8, 3; 4) and phase 2 (8, 5; 4); pair updates (the iterate
-// updated every second iteration): 22 -> as 18, 23 -> as 20
+// phase 2 (8, 4; 4), 21 -> phase 1 (8, 3; 4) and phase 2 (8, 5; 4); grouped iterate updates (x
+// updated every m-th iteration): 22 -> as 18 with m = 2, 23 -> as 20 with m = 2, 24 -> as 18 with m = 4
 int tma_config_by(int cfg) {
   return (cfg == 2 || cfg == 3 || cfg == 4 || cfg == 5 || cfg == 12 || cfg == 16) ? 16 : 8;
 }
 
-bool tma_config_xpair(int cfg) { return cfg == 22 || cfg == 23; }
+int tma_config_xsteps(int cfg) { return (cfg == 22 || cfg == 23) ? 2 : cfg == 24 ? 4 : 1; }
 
 cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st) {
   if (b.nitems <= 0) return cudaSuccess;
@@ -167,11 +167,13 @@ cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T,
   WRI_WSE_CASE(M_P2, 20, 8, 4, 4)
   WRI_WSE_CASE(M_P1, 21, 8, 3, 4)
   WRI_WSE_CASE(M_P2, 21, 8, 5, 4)
-  // pair updates: the same kernels as 18 and 20, with b.xpair set by the caller
+  // grouped updates: the same kernels as 18 and 20, with b.xsteps set by the caller
   WRI_WSE_CASE(M_P1, 22, 8, 3, 4)
   WRI_WSE_CASE(M_P2, 22, 8, 3, 4)
   WRI_WSE_CASE(M_P1, 23, 8, 3, 4)
   WRI_WSE_CASE(M_P2, 23, 8, 4, 4)
+  WRI_WSE_CASE(M_P1, 24, 8, 3, 4)
+  WRI_WSE_CASE(M_P2, 24, 8, 3, 4)
 #undef WRI_WSE_CASE
   return cudaErrorInvalidValue;
 }

@@ -61,6 +61,6 @@ struct TmaSet;
 // TMA-pipelined phase 1 / phase 2 kernels (complex64); cfg selects tile height and stages.
 int tma_config_count();
 int tma_config_by(int cfg);
-bool tma_config_xpair(int cfg);  // phase 1 updates the iterate every second iteration
+int tma_config_xsteps(int cfg);  // iterations per iterate update of phase 1 (1, 2 or 4)
 cudaError_t launch_phase_tma(int mode, int cfg, const Batch& b, const TmaSet& T, int grid, cudaStream_t st);
 }  // namespace wri

@@ -53,7 +53,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
   for (int k = rb + tid; k < re; k += NT) {
     const long long node = off + b.rec_idx[k];
     if (MODE == M_P1) {
-      const C pn = ldcg_c((const C*)G.p[cur ^ 1] + node);
+      const C pn = ldcg_c((const C*)G.p[pslot(b, sd->iter)] + node);
       rec += (double)lam * (double)lam * (double)abs2(pn);
     } else if (MODE == M_SH && G.rmap) {
       // the receiver terms were added in the stencil pass (refinement): nothing left to do
@@ -76,26 +76,28 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     const double tot = part + rec;
     if (MODE == M_P1) {
       const double delta = tot;
-      const double a_prev = sd->alpha;
       double alpha = 0.0;
+      sd->delta = delta;
       if (!(delta > 0.0) || !isfinite(delta)) {
         sd->status = isfinite(delta) ? WRI_SYS_BREAKDOWN : WRI_SYS_NONFINITE;
-        if (b.xpair && (sd->iter & 1)) {
-          // pair updates: this odd iteration left the previous step pending; the x-only pass
-          // adds it (step a_prev, direction in the buffer this iteration read p_old from)
-          alpha = a_prev;
+        if (sd->iter % xsteps_of(b) != 0) {
+          // grouped updates: steps of earlier iterations are still pending (this pass added none);
+          // the step history is left as it is, newest = the previous iteration's, and the x-only
+          // pass adds them
           sd->state = ST_FINISHING;
         } else {
           sd->state = ST_DONE;
+          sd->alpha = 0.0;
           atomicSub(b.remaining, 1);
         }
       } else {
         alpha = sd->gamma / delta;
+        sd->alpha_hist[2] = sd->alpha_hist[1];
+        sd->alpha_hist[1] = sd->alpha_hist[0];
+        sd->alpha_hist[0] = sd->alpha;
+        sd->alpha = alpha;
       }
-      sd->delta = delta;
-      sd->alpha_prev = a_prev;
-      sd->alpha = alpha;
-      *bcast = sd->state == ST_ACTIVE ? alpha : 0.0;  // step of the receiver residual (none on breakdown)
+      *bcast = alpha;  // step of the receiver residual (none on breakdown)
     } else if (MODE == M_P2) {
       const double g = tot;
       const int it = sd->iter + 1;
@@ -129,7 +131,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
         sd->gamma = g;
         sd->beta = 0.0;
         sd->alpha = 0.0;
-        sd->alpha_prev = 0.0;
+        sd->alpha_hist[0] = sd->alpha_hist[1] = sd->alpha_hist[2] = 0.0;
         sd->iter = 0;
         sd->iter_total = 0;
         sd->tol = b.tol;
@@ -176,7 +178,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
           sd->tol = fmax(b.inner_tol, 0.95 * b.refine_tol * sd->snorm_b / rn);
           sd->beta = 0.0;
           sd->alpha = 0.0;
-          sd->alpha_prev = 0.0;
+          sd->alpha_hist[0] = sd->alpha_hist[1] = sd->alpha_hist[2] = 0.0;
           sd->iter = 0;
           sd->state = ST_ACTIVE;
           atomicAdd(b.remaining, 1);
@@ -191,7 +193,7 @@ __device__ void finalize(const Batch& b, const GroupDev& G, SysDev* sd, int sl, 
     if (a != 0.0) {
       for (int k = rb + tid; k < re; k += NT) {
         const long long node = off + b.rec_idx[k];
-        const C pn = ldcg_c((const C*)G.p[cur ^ 1] + node);
+        const C pn = ldcg_c((const C*)G.p[pslot(b, sd->iter)] + node);
         r2[k] = r2[k] - R(a * (double)lam) * pn;
       }
     }

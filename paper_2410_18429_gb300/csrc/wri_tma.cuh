@@ -22,8 +22,14 @@
 
 namespace wri {
 
-// halo boxes of s, p, t1, r1; 32 x BY boxes of x and (pair updates) of p; the model
-enum TmaMap : int { TM_S = 0, TM_P0, TM_P1, TM_X, TM_T1, TM_R0, TM_R1, TM_M, TM_PC0, TM_PC1, TM_COUNT };
+// halo boxes of s, t1, r1 and of the p slots; 32 x BY boxes of x and (grouped iterate updates) of
+// the p slots; the model
+enum TmaMap : int {
+  TM_S = 0, TM_X, TM_T1, TM_R0, TM_R1, TM_M,
+  TM_P0, TM_P1, TM_P2, TM_P3,
+  TM_PC0, TM_PC1, TM_PC2, TM_PC3,
+  TM_COUNT
+};
 
 struct TmaSet {
   CUtensorMap map[WRI_MAXG][TM_COUNT];
@@ -729,10 +735,11 @@ struct WsLayout {
   static constexpr int OFF_X = OFF_B + pad(HALO);
   static constexpr int OFF_M = OFF_X + (MODE == M_P1 ? pad(CTR) : 0);
   static constexpr int STAGE = OFF_M + pad(MB);
-  // pair updates (phase 1): p of two iterations back, in a box appended to each stage
+  // grouped iterate updates (phase 1): the older directions of the group, in boxes appended to
+  // each stage (box i at OFF_X2 + i X2)
   static constexpr int OFF_X2 = STAGE;
   static constexpr int X2 = (MODE == M_P1) ? pad(CTR) : 0;
-  static size_t bytes(int S, bool xpair) { return 128 + (size_t)S * (STAGE + (xpair ? X2 : 0)) + 16 * S; }
+  static size_t bytes(int S, int extra) { return 128 + (size_t)S * (STAGE + extra * X2) + 16 * S; }
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -779,14 +786,17 @@ __device__ __forceinline__ float2 fma_c(float c, float2 b, float2 a) {
 // partial value and the z+1 coefficient stay in registers), then releases the stage at once:
 // S - 1 planes of copies stay in flight instead of S - 2.
 //
-// b.xpair = 1 ("pair updates", phase 1 only): the iterate is updated every second
-// iteration, x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1} in iteration k = 2, 4, ...  p_{k-2}
-// still lies in the buffer that iteration k overwrites with p_k (each thread reads its own nodes
-// there before it writes them), so odd iterations read and write no x and even ones read one
-// extra vector: 44 instead of 48 bytes per node-system in phase 1, averaged over two iterations.
-// The x-only pass of a finishing system adds whatever is pending.  A run-time switch of the same
-// kernel, so the stencil and the reductions are the same machine code with and without it; each
-// stage then holds one more 32 x BY box (the launch sizes the shared memory for it).
+// b.xsteps = m > 1 ("grouped iterate updates", phase 1 only): x is needed only at the end of a
+// solve, so phase 1 updates it every m-th iteration, x += alpha_{k-m} p_{k-m} + ... +
+// alpha_{k-1} p_{k-1} in iteration k = m, 2m, ...  The directions live in a ring of R slots (R = 2
+// for m = 2, 4 for m = 4, p_j in slot (j + 1) mod R): p_{k-1} is the stencil input anyway, the older
+// m - 1 arrive in 32 x BY boxes, and p_{k-m} lies in the slot iteration k overwrites with p_k (each
+// thread reads its own nodes there before it writes them).  Phase 1 moves 32 bytes per
+// node-system in the other iterations and 32 + 16 + 8 (m - 1) in the updating one: 44 (m = 2) or
+// 42 (m = 4) instead of 48 on average.  The steps are added oldest first, so x rounds exactly as
+// with one update per iteration.  The x-only pass of a finishing system adds whatever is pending.
+// A run-time switch of the same kernel (the stencil and reduction code is the same machine code
+// with and without it); each stage then holds m - 1 more boxes (the launch sizes the shared memory).
 template <int MODE, int BY, int S, int MINB, bool PW = true, bool ER = false>
 __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(const __grid_constant__ Batch b,
                                                                              const __grid_constant__ TmaSet T) {
@@ -795,8 +805,8 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
   static_assert(PW || !ER, "early release is built with the copy warp");
   typedef float2 C;
   typedef WsLayout<MODE, BY> L;
-  const bool XP = (MODE == M_P1) && b.xpair != 0;
-  const int SB = L::STAGE + (XP ? L::X2 : 0);  // bytes of one stage
+  const int XS = (MODE == M_P1) ? xsteps_of(b) : 1;  // iterations per iterate update
+  const int SB = L::STAGE + (XS - 1) * L::X2;          // bytes of one stage
   typedef FirstThreadsSync<16 * BY> CSync;
   constexpr bool CONJ = (MODE == M_P2);
   constexpr int NC = 16 * BY;   // consumer threads: two x-adjacent nodes each
@@ -853,10 +863,10 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
       const int cur = iter & 1;
       const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
       const bool hasB = (MODE == M_P2) || iter > 0;
-      const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
-      const bool hasX = (MODE == M_P1) && (XP ? (iter >= 2 && !(iter & 1)) : iter > 0);
-      const bool hasX2 = XP && hasX;
-      const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + (hasX2 ? L::CTR : 0) + L::MB;
+      const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? TM_P0 + pslot(b, iter - 1) : TM_T1];
+      const bool hasX = (MODE == M_P1) && iter >= XS && iter % XS == 0;
+      const int nX2 = hasX ? XS - 1 : 0;  // older directions of the group: p_{iter-XS} .. p_{iter-2}
+      const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + nX2 * L::CTR + L::MB;
       const int count = z1 - z0 + 2;
       for (int q = 0; q < count; ++q, ++fills) {
         const int st = (int)(fills % S);
@@ -879,7 +889,9 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasX) tma_load_4d(base + L::OFF_X, &T.map[gi][TM_X], x0, y0, kq, sl, &full[st]);
-        if (hasX2) tma_load_4d(base + L::OFF_X2, &T.map[gi][cur ? TM_PC0 : TM_PC1], x0, y0, kq, sl, &full[st]);
+        for (int i = 0; i < nX2; ++i)
+          tma_load_4d(base + L::OFF_X2 + i * L::X2, &T.map[gi][TM_PC0 + pslot(b, iter - XS + i)], x0, y0, kq, sl,
+                      &full[st]);
         tma_load_3d(base + L::OFF_M, &T.map[gi][TM_M], x0, y0, kq, &full[st]);
       }
     }
@@ -926,36 +938,38 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
     double accd = 0.0;
 
     if (xonly) {
+      // the steps not yet in x: those of iterations iter - c .. iter - 1, oldest first (c = 1 with
+      // one update per iteration; grouped updates: the rest of the last group, or on a breakdown
+      // the steps before it)
       C* X = (C*)G.x + off + col;
-      const C* Pc = (const C*)G.p[cur] + off + col;
-      const float a = (float)sd->alpha;
-      // pair updates: after an odd number of iterations two steps are pending; the older
-      // direction lies in the other p buffer
-      const bool two = XP && !(iter & 1);
-      const C* Po = (const C*)G.p[cur ^ 1] + off + col;
-      const float a2 = (float)sd->alpha_prev;
+      const int c = (iter - 1) % XS + 1;
       if (own)
         for (int k = z0; k < z1; ++k) {
           const long long q = k * plane;
           float4 xv = ld4(X + q);
-          if (two) {
-            const float4 ov = __ldg(reinterpret_cast<const float4*>(Po + q));
-            xv = make_float4(__fmaf_rn(a2, ov.x, xv.x), __fmaf_rn(a2, ov.y, xv.y), __fmaf_rn(a2, ov.z, xv.z),
-                             __fmaf_rn(a2, ov.w, xv.w));
+          for (int jj = c - 1; jj >= 0; --jj) {
+            const float a = (float)(jj == 0 ? sd->alpha : sd->alpha_hist[jj - 1]);
+            const C* Pj = (const C*)G.p[pslot(b, iter - 1 - jj)] + off + col;
+            const float4 pv = __ldg(reinterpret_cast<const float4*>(Pj + q));
+            // explicit fma (as in the iteration's own update): the rounding must not depend on how
+            // the compiler contracts this instantiation
+            xv = make_float4(__fmaf_rn(a, pv.x, xv.x), __fmaf_rn(a, pv.y, xv.y), __fmaf_rn(a, pv.z, xv.z),
+                             __fmaf_rn(a, pv.w, xv.w));
           }
-          // explicit fma (as in the iteration's own update): the rounding must not depend on how
-          // the compiler contracts this instantiation
-          const float4 pv = __ldg(reinterpret_cast<const float4*>(Pc + q));
-          st4(X + q, fma_c(a, lo2(pv), lo2(xv)), fma_c(a, hi2(pv), hi2(xv)));
+          st4(X + q, lo2(xv), hi2(xv));
         }
     } else {
       const bool hasB = (MODE == M_P2) || iter > 0;
-      const bool hasX = (MODE == M_P1) && (XP ? (iter >= 2 && !(iter & 1)) : iter > 0);
-      const bool hasX2 = XP && hasX;
+      const bool hasX = (MODE == M_P1) && iter >= XS && iter % XS == 0;
+      const int nX2 = hasX ? XS - 1 : 0;
       const float coef = (MODE == M_P1) ? (float)sd->beta : -(float)sd->alpha;
       const float xal = (float)sd->alpha;
-      const float xal2 = (float)sd->alpha_prev;
-      C* pF = ((MODE == M_P1) ? (C*)G.p[cur ^ 1] : (C*)G.r1[cur ^ 1]) + off + col;
+      // steps of the older directions in the update boxes: box i holds p_{iter-XS+i}
+      float xh[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < nX2) xh[i] = (float)sd->alpha_hist[XS - 2 - i];
+      C* pF = ((MODE == M_P1) ? (C*)G.p[pslot(b, iter)] : (C*)G.r1[cur ^ 1]) + off + col;
       C* pX = (C*)G.x + off + col;
       C* pO = ((MODE == M_P1) ? (C*)G.t1 : (C*)G.s) + off + col;
       const C* pG = (MODE == M_P2 && G.gvec) ? (const C*)G.gvec + off + col : nullptr;
@@ -980,15 +994,17 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
         }
         if (s_abort) return;
         const CUtensorMap* mapA = &T.map[gi][MODE == M_P1 ? TM_S : (cur ? TM_R1 : TM_R0)];
-        const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? (cur ? TM_P1 : TM_P0) : TM_T1];
-        const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + (hasX2 ? L::CTR : 0) + L::MB;
+        const CUtensorMap* mapB = &T.map[gi][MODE == M_P1 ? TM_P0 + pslot(b, iter - 1) : TM_T1];
+        const uint32_t tx_bytes = L::HALO + (hasB ? L::HALO : 0) + (hasX ? L::CTR : 0) + nX2 * L::CTR + L::MB;
         unsigned char* base = smem + (size_t)st * SB;
         const int kq = z0 - 1 + q;
         mbar_expect_tx(&full[st], tx_bytes);
         tma_load_4d(base, mapA, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasB) tma_load_4d(base + L::OFF_B, mapB, x0 - 2, y0 - 1, kq, sl, &full[st]);
         if (hasX) tma_load_4d(base + L::OFF_X, &T.map[gi][TM_X], x0, y0, kq, sl, &full[st]);
-        if (hasX2) tma_load_4d(base + L::OFF_X2, &T.map[gi][cur ? TM_PC0 : TM_PC1], x0, y0, kq, sl, &full[st]);
+        for (int i = 0; i < nX2; ++i)
+          tma_load_4d(base + L::OFF_X2 + i * L::X2, &T.map[gi][TM_PC0 + pslot(b, iter - XS + i)], x0, y0, kq, sl,
+                      &full[st]);
         tma_load_3d(base + L::OFF_M, &T.map[gi][TM_M], x0, y0, kq, &full[st]);
         issued = u + 1;
       };
@@ -1058,11 +1074,14 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
               v1 = fma_c(coef, hi2(bb), v1);
               if (MODE == M_P1 && hasX && mine) {
                 float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
-                if (hasX2) {
-                  // the older step first: the same order as two single updates
-                  const float4 ov = ld4(reinterpret_cast<const C*>(base + L::OFF_X2) + oc);
-                  xv = make_float4(__fmaf_rn(xal2, ov.x, xv.x), __fmaf_rn(xal2, ov.y, xv.y), __fmaf_rn(xal2, ov.z, xv.z),
-                                   __fmaf_rn(xal2, ov.w, xv.w));
+                // the older steps first: the same order as single updates
+                #pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                  if (e >= nX2) break;
+                  const float4 ov = ld4(reinterpret_cast<const C*>(base + L::OFF_X2 + e * L::X2) + oc);
+                  const float h = xh[e];
+                  xv = make_float4(__fmaf_rn(h, ov.x, xv.x), __fmaf_rn(h, ov.y, xv.y), __fmaf_rn(h, ov.z, xv.z),
+                                   __fmaf_rn(h, ov.w, xv.w));
                 }
                 st4(pX + po, fma_c(xal, lo2(bb), lo2(xv)), fma_c(xal, hi2(bb), hi2(xv)));
               }
@@ -1203,11 +1222,14 @@ __global__ void __launch_bounds__(16 * BY + (PW ? 32 : 0), MINB) k_phase_ws(cons
             v1 = fma_c(coef, hi2(bb), v1);
             if (MODE == M_P1 && hasX && mine) {
               float4 xv = ld4(reinterpret_cast<const C*>(base + L::OFF_X) + oc);
-              if (hasX2) {
-                // the older step first: the same order as two single updates
-                const float4 ov = ld4(reinterpret_cast<const C*>(base + L::OFF_X2) + oc);
-                xv = make_float4(__fmaf_rn(xal2, ov.x, xv.x), __fmaf_rn(xal2, ov.y, xv.y), __fmaf_rn(xal2, ov.z, xv.z),
-                                 __fmaf_rn(xal2, ov.w, xv.w));
+              // the older steps first: the same order as single updates
+              #pragma unroll
+              for (int e = 0; e < 3; ++e) {
+                if (e >= nX2) break;
+                const float4 ov = ld4(reinterpret_cast<const C*>(base + L::OFF_X2 + e * L::X2) + oc);
+                const float h = xh[e];
+                xv = make_float4(__fmaf_rn(h, ov.x, xv.x), __fmaf_rn(h, ov.y, xv.y), __fmaf_rn(h, ov.z, xv.z),
+                                 __fmaf_rn(h, ov.w, xv.w));
               }
               st4(pX + po, fma_c(xal, lo2(bb), lo2(xv)), fma_c(xal, hi2(bb), hi2(xv)));
             }

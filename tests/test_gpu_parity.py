@@ -88,10 +88,10 @@ def test_fixed_iterations_match_oracle_cgls(W, dtype, tol, source_free):
         assert abs(rr.cpu().numpy()[s] - rr_k) <= max(tol, 1e-6) * rr_k * 10
 
 
-@pytest.mark.parametrize("cfg", list(range(24)))
+@pytest.mark.parametrize("cfg", list(range(25)))
 @pytest.mark.parametrize("source_free", [True, False])
 def test_tma_phases_match_oracle_and_march(W, cfg, source_free):
-    """TMA-pipelined phases (x extent a multiple of 4; configurations 9-23 are the
+    """TMA-pipelined phases (x extent a multiple of 4; configurations 9-24 are the
     warp-specialised kernels): ragged 32 x BY tiles, iterates of k CGLS steps equal the
     oracle's and the z-march kernels' (same tile height)."""
     G = case(nphys=(36, 13, 10), npml=4, nsys=3)
@@ -157,14 +157,14 @@ def test_interior_tiles_tma_match_oracle(W, cfg, order, zsplit):
         assert 0 < rr[s] and abs(rr[s] - rr_k) <= 3e-3 * rr_k, (s, rr[s], rr_k)
 
 
-@pytest.mark.parametrize("pair,single", [(22, 18), (23, 20)])
+@pytest.mark.parametrize("pair,single", [(22, 18), (23, 20), (24, 18)])
 def test_pair_updates_equal_single_updates(W, pair, single):
-    """Pair configurations update the iterate every second iteration, adding the older step first,
-    so they round exactly like one update per iteration.  On the grid with interior tiles the
-    wavefields, residuals and iteration counts equal the single-update configuration's bit for bit:
-    after an even and an odd number of iterations (one or two steps pending at the end), for solves
-    stopped by their tolerance (systems ending on different iterations), and for the inner solves
-    of an FP64 refinement."""
+    """Grouped-update configurations update the iterate every second (22, 23) or fourth (24)
+    iteration, adding the older steps first, so they round exactly like one update per iteration.
+    On the grid with interior tiles the wavefields, residuals and iteration counts equal the
+    single-update configuration's bit for bit: after 24 to 27 iterations (every count of pending
+    steps at the end), for solves stopped by their tolerance (systems ending on different
+    iterations), and for the inner solves of an FP64 refinement."""
     import torch
     G = _interior_case()
 
@@ -176,7 +176,7 @@ def test_pair_updates_equal_single_updates(W, pair, single):
         u = (spec.u64 if spec.u64 is not None else spec.u).cpu().numpy()
         return u, rr.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
 
-    cases = [dict(tol=0.0, max_iter=24), dict(tol=0.0, max_iter=25), dict(tol=1e-3, max_iter=100000),
+    cases = [dict(tol=0.0, max_iter=k) for k in (24, 25, 26, 27)] + [dict(tol=1e-3, max_iter=100000),
              dict(tol=1e-6, max_iter=100000, max_refine=3, refine_tol=1e-6, inner_tol=1e-3, refined=True)]
     for kw in cases:
         a, b = run(pair, **dict(kw)), run(single, **dict(kw))
@@ -503,7 +503,7 @@ def test_autotune_choice_solves_like_default_and_is_cached(W):
     s1, s2 = _spec(W, G1, 0), _spec(W, G2, 0)
     base = W.make_opts(tol=0.0, max_iter=20, dtype=0)
     tuned = W.autotune([s1, s2], base, trial_iters=6)
-    assert tuned.kernel in [2 + c for c in (8, 9, 12, 13, 17, 18, 22)] and tuned.order in (2, 5, 6)
+    assert tuned.kernel in [2 + c for c in (8, 9, 12, 13, 17, 18, 22, 24)] and tuned.order in (2, 5, 6)
     s1.u.fill_(3.0)
     again = W.autotune([s1, s2], base, trial_iters=6)
     assert (again.kernel, again.order) == (tuned.kernel, tuned.order)
