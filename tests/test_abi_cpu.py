@@ -85,6 +85,25 @@ def test_workspace_size_validation(W):
     assert W.workspace_size([_spec(W)], W.make_opts(max_refine=3, dtype=W.C128)) == 0
 
 
+def test_direction_ring_in_the_workspace(W):
+    """Configuration 24 (x updated every fourth iteration) keeps four search directions per system;
+    the automatic kernel choice reserves them too, so that wri_autotune may pick it in a workspace
+    sized before tuning. The other configurations, and batches the TMA phases cannot take, keep two.
+    Kernel indices past the last configuration are rejected."""
+    n = 20 * 18 * 16
+    vec = 2 * n * 8  # one complex64 vector of the 2 systems (a multiple of the 256-byte alignment)
+
+    def size(spec, kernel):
+        return W.workspace_size([spec], W.make_opts(kernel=kernel))
+
+    auto, quad, single, pair = (size(_spec(W), k) for k in (0, W.KERNEL_TMA(24), W.KERNEL_TMA(18), W.KERNEL_TMA(22)))
+    assert single > 0 and pair == single
+    assert auto == quad == single + 2 * vec
+    odd = _spec(W, nx=22)  # x extent not a multiple of 4: z-march kernels whatever the request
+    assert size(odd, 0) == size(odd, W.KERNEL_TMA(24)) > 0
+    assert size(_spec(W), W.KERNEL_TMA(24) + 1) == 0
+
+
 def test_solve_rejects_before_device_work(W):
     o = W.make_opts()
     m = W._Marshal([_spec(W, rec_idx=np.array([10, 20, 10, 40, 50]))])
