@@ -64,6 +64,10 @@ def parse():
                    help="comma-separated systems per call (e.g. 1,2,4,8,16,32): instead of the bench line, time "
                         "one CGLS iteration of that many systems of the 148^3 group in one batched call and "
                         "print one JSON line for each (the grouping sweep of Eq. Mmatrix2)")
+    p.add_argument("--camembert-shape", action="store_true",
+                   help="instead of the bench line, time one misfit + gradient evaluation on the shape of the "
+                        "paper's timing case (61^3 nodes, 9 sources, 2025 receivers, 5 Hz, residual 1e-6) with "
+                        "n_b = 9, 4 and 1 systems per call, and print one JSON line")
     return p.parse_args()
 
 
@@ -307,6 +311,100 @@ def run_group_sweep(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def run_camembert_shape(args):
+    """One misfit + gradient evaluation on the shape of the paper's timing case (Sec. "Evaluation of
+    GPU Acceleration Efficiency", Table CMPTime: a 3 km cube at h = 50 m, 61^3 nodes, 9 sources,
+    2025 receivers, 5 Hz, relative residual 1e-6), with synthetic model and data on a 10-cell
+    absorbing layer (81^3 computational nodes), and on the nearest cube whose x extent the TMA phases
+    take (60^3 + layer, 80^3).  Certified precision configuration, refined to an
+    FP64 normal-equation residual of 1e-6 (every system must end with status OK).  The 9 systems
+    are evaluated in batched calls of n_b systems (9, 4 and 1, so 1, 3 and 9 calls), each call a
+    solve, a source estimate and a gradient, after one untimed evaluation; CUDA events on the
+    launching stream, SM clocks sampled.  Prints one JSON line per grid."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    for nphys in (61, 60):
+        camembert_case(args, synth.workload_camembert_shape(nphys), dev, stream)
+
+
+def camembert_case(args, G, dev, stream):
+    """The evaluations of run_camembert_shape on one grid (61^3 physical: x extent 81, z-march
+    kernels; 60^3: x extent 80, TMA phases)."""
+    import torch
+
+    import synth
+    from paper_2410_18429_gb300 import wri
+    from paper_2410_18429_gb300.problem import to_device
+
+    def part(a, b):
+        return synth.Group(G.spec, G.freq, G.v, G.src[a:b], G.rec_off[a:b + 1] - G.rec_off[a],
+                           G.rec_idx[G.rec_off[a]:G.rec_off[b]], G.lam, G.v_max, G.pml_R, G.alpha[a:b],
+                           G.d[G.rec_off[a]:G.rec_off[b]])
+
+    opts = solve_opts(wri, args, iters=400000, max_refine=8, refine_tol=1e-6, inner_tol=1e-3)
+    full = with_u64([to_device(G, wri.C64, dev)], dev)
+    work = torch.empty(wri.workspace_size(full, opts), dtype=torch.uint8, device=dev)
+    if int(opts.kernel) == 0:
+        opts = wri.autotune(full, opts, trial_iters=8, workspace=work)
+    grad = torch.zeros(G.spec.nz, G.spec.ny, G.spec.nx, dtype=torch.float64, device=dev)
+    f = torch.zeros(1, dtype=torch.float64, device=dev)
+    runs = []
+    for nb in (9, 4, 1):
+        calls = []
+        for a in range(0, G.nsys, nb):
+            sp = with_u64([to_device(part(a, min(a + nb, G.nsys)), wri.C64, dev)], dev)
+            calls.append((sp, torch.empty(wri.workspace_size(sp, opts), dtype=torch.uint8, device=dev)))
+
+        def evaluate():
+            out = []
+            grad.zero_()
+            f.zero_()
+            for sp, w in calls:
+                for s_ in sp:
+                    s_.u.zero_()
+                    s_.u64.zero_()
+                it, rr, st = wri.solve(sp, opts, workspace=w)
+                wri.source_estimate(sp, wri.C64, workspace=w)
+                wri.gradient_refined(sp, opts, w, grads=[grad], f=f)
+                out.append((it, rr, st))
+            return out
+
+        evaluate()
+        torch.cuda.synchronize()
+        clk = Clocks(0)
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = evaluate()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        its = torch.cat([r[0] for r in res]).cpu().tolist()
+        rrs = torch.cat([r[1] for r in res]).cpu().tolist()
+        sts = torch.cat([r[2] for r in res]).cpu().tolist()
+        runs.append({"n_b": nb, "calls": len(calls), "seconds": e0.elapsed_time(e1) / 1e3, "iters": its,
+                     "fp64_relres_max": max(rrs), "status_all_ok": all(v == wri.SYS_OK for v in sts),
+                     "f": float(f.item()), "clocks": clocks})
+    g = G.spec
+    print(json.dumps({"camembert_shape": {
+        "grid": f"{g.nx}x{g.ny}x{g.nz} computational nodes ({g.nx - 2 * g.npml}^3 physical + {g.npml}-cell layer), "
+                f"h = {g.h} m",
+        "phase_kernels": "TMA" if g.nx % 4 == 0 else "z-march (x extent not a multiple of 4)",
+        "freq_hz": G.freq, "systems": int(G.nsys), "receivers_per_system": int(G.rec_off[1] - G.rec_off[0]),
+        "precision": "complex64 CGLS inside FP64 iterative refinement to an FP64 normal-equation residual of 1e-6; "
+                     "FP64 source estimate and gradient from the refinement's residual",
+        "kernel": {"config": int(opts.kernel) - 2 if int(opts.kernel) >= 2 else None, "order": int(opts.order)},
+        "data": "synthetic (Gaussian anomaly in 2500 m/s; homogeneous Green's-function traces)",
+        "runs": runs, "library": wri.version()}}))
+
+
 def solve_opts(wri, args, certified=True, iters=None, **kw):
     """Options of the bench step.  certified: the precision configuration whose converged results
     meet the stated accuracy (complex64 CGLS with FP32 stencils and FP64 reductions inside FP64
@@ -390,6 +488,9 @@ def main():
         return
     if args.group_sweep:
         run_group_sweep(args)
+        return
+    if args.camembert_shape:
+        run_camembert_shape(args)
         return
     import numpy as np
     import torch

@@ -342,10 +342,11 @@ def workload_c5(nsrc: int = 64) -> Group:
     return grp
 
 
-def workload_camembert_shape() -> Group:
+def workload_camembert_shape(nphys: int = 61) -> Group:
     """Shape of the Camembert timing case: 3 km cube, h=50 (61^3) + 10 PML, 9 sources
-    at z=0.35 km, 45x45 receivers at z=2.3 km, 5 Hz; velocities are our choice."""
-    g = grid(61, 10, 50.0)
+    at z=0.35 km, 45x45 receivers at z=2.3 km, 5 Hz; velocities are our choice.  ``nphys`` = 60
+    gives the nearest cube with an x extent (80) that is a multiple of 4."""
+    g = grid(nphys, 10, 50.0)
     v = velocity_gaussian_anomaly(g, 2500.0, amp=0.1, sigma_cells=8.0, seed=7, lo=25, hi=35)
     src = surface_sources(g, (10, 30, 50), (10, 30, 50), 7)
     rx = np.linspace(8, 52, 45).round().astype(int)
