@@ -404,6 +404,33 @@ def test_pipeline_gradient_matches_oracle(W):
     assert abs(f.item() - f_ex) <= 1e-4 * abs(f_ex)
 
 
+@pytest.mark.parametrize("cfg", [18, 24])
+def test_certified_pipeline_on_tma_phases_matches_oracle(W, cfg):
+    """The certified configuration of the benchmark on the TMA phases (x extent 24, a multiple of 4):
+    complex64 CGLS with x updated every iteration (configuration 18) or every fourth (24) inside
+    FP64 refinement, the FP64 source estimate, and the gradient read off the refinement's FP64
+    residual, against the oracle's exact evaluation of f4 and g4: wavefield and weights to 1e-5,
+    gradient and objective to 1e-4."""
+    G = case(nphys=(18, 12, 9), npml=3, nsys=3, freq=14.0)
+    m, d, _ = seen(G, True)
+    spec = _spec(W, G, 0)
+    spec.u64 = torch.zeros(G.nsys, G.spec.n, dtype=torch.complex128, device="cuda")
+    opts = W.make_opts(tol=1e-3, max_iter=200000, dtype=0, max_refine=12, refine_tol=1e-10, inner_tol=1e-3,
+                       kernel=W.KERNEL_TMA(cfg))
+    work = torch.empty(W.workspace_size([spec], opts), dtype=torch.uint8, device="cuda")
+    it, rr, st = W.solve([spec], opts, workspace=work)
+    assert st.cpu().tolist() == [W.SYS_OK] * 3
+    assert 0 < float(rr.max()) <= 1e-10
+    a = W.source_estimate([spec], 0, workspace=work)
+    (g,), f = W.gradient_refined([spec], opts, work)
+    u_ex, a_ex, f_ex, g_ex = O.evaluate(G.spec.shape, G.spec.h, G.omega, m, G.spec.npml, G.v_max, G.src,
+                                        G.rec_off, G.rec_idx, d, G.lam)
+    assert rel(spec.u64.cpu().numpy(), u_ex) < 1e-5
+    assert rel(a.cpu().numpy(), a_ex) < 1e-5
+    assert rel(g.cpu().numpy().ravel(), g_ex) < 1e-4
+    assert abs(f.item() - f_ex) <= 1e-4 * abs(f_ex)
+
+
 @pytest.mark.parametrize("source_free", [True, False])
 def test_gradient_from_refined_residual_equals_stencil_gradient(W, source_free):
     """wri_gradient_refined reads the FP64 residual a refined solve leaves in its workspace: the same f
