@@ -63,3 +63,24 @@ def test_clock_sampler_parses_speeds_and_throttle_reasons(tmp_path):
     assert not os.path.exists(c.path)
     c2 = bench.Clocks(0)
     assert c2.stop()["reasons"] == ["nvidia-smi unavailable"]       # sampler never started
+
+
+def test_algorithmic_bytes_per_node_system_by_configuration():
+    """The roofline's byte model of one CGLS iteration per node and system: phase 1 reads s, p_old
+    and writes p, t1 (32 B) plus x in and out (16 B) when it updates x, and m - 1 older directions
+    (8 B each) in the iteration that adds the steps of m iterations; phase 2 reads r1, t1 and writes
+    r1, s (32 B).  One update per iteration: 80 B; every second iteration (configurations 22, 23):
+    76 B; every fourth (24): 74 B."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def b(kernel):
+        return bench.bytes_per_node_sys(types.SimpleNamespace(kernel=kernel))
+
+    for m, cfgs in ((1, (8, 9, 18, 20, 21)), (2, (22, 23)), (4, (24,))):
+        per_iter = 32 + 32 + (16 + 8 * (m - 1)) / m
+        for c in cfgs:
+            assert b(2 + c) == per_iter, (c, b(2 + c), per_iter)
+    assert b(0) == b(1) == 80.0
+    assert (b(2 + 18), b(2 + 22), b(2 + 24)) == (80.0, 76.0, 74.0)
